@@ -1,0 +1,353 @@
+"""Benchmark: complex double-double f + Jacobian evaluations per second.
+
+Workload (one "step" = one evaluation of f and the full Jacobian at a batch
+of points, i.e. the whole hot path: power table, common factors, Speelpenning
+gradients, coefficient products and sums):
+  n = 32 variables, 32 polynomials, m = 64 monomials each, k = 9 variables
+  per monomial, exponents 1..5, unit-circle complex double-double
+  coefficients and points, 1024 points per GPU (seeded synthetic data).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  With N > 1 (launched by torch.distributed.run) every
+rank evaluates its own batch of 1024 points on its own GPU (weak scaling, no
+collective on the data path); the reported time is the maximum over ranks and
+`value` counts the points of all ranks.  `--impl reference` times the CPU
+double-double oracle on the host cores on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "complex-dd f+Jacobian evals/s on 1 GB300; %FP64 peak; dd/FP64 time ratio"
+CONFIG_INDEX = 2
+WORKLOAD = ("n=32 variables, 32 polynomials, m=64 monomials, k=9, exponents 1..5, unit-circle complex "
+            "double-double coefficients and points, 1024 points per GPU")
+L2_FLUSH_BYTES = 256 << 20
+SMS = 152
+DFMA_PER_SM_CLK = 2  # nominal FP64 FMA lanes per SM per clock on GB300
+# DRAM bytes (read + write) of one main-kernel launch on this workload, from the ncu capture
+# summarised in profiles/main_kernel_dd_config2.md; set to None when the kernel changes.
+MAIN_KERNEL_DRAM_BYTES = 4.372992e6 + 4.352e3
+
+
+def env_dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def rank_points_seed(rank: int) -> int:
+    """Each rank evaluates its own batch: the points seed depends on the rank."""
+    return synth.SEED_BASE + CONFIG_INDEX + 1000 + 7919 * rank
+
+
+def max_over_ranks(value: float, dist) -> float:
+    """Largest value over all ranks (timings: the slowest rank sets the time)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, points_per_rank: int, ms_per_step: float) -> float:
+    """Evaluations per second of the whole job (weak scaling: every rank has its own points)."""
+    return world * points_per_rank / (ms_per_step * 1e-3)
+
+
+def peaks_file():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.lines = []
+        self.proc = None
+        self.windows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", str(self.period)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self, t0, t1):
+        rows = []
+        for ts, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[4:]))
+            except ValueError:
+                continue
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        window = "timed region"
+        if not inside:  # timed region shorter than the sampling period: nearest samples under the same load
+            inside = sorted(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))[:3]
+            window = "nearest samples to the timed region"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in inside:
+            for name, val in zip(names, r[3][1:]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
+
+
+def cpu_oracle_rate(system, pts, seconds: float = 10.0, max_points=None):
+    """The C double-double oracle on the host cores: evaluations per second,
+    repeating the batch (or its first max_points points) for ~`seconds`."""
+    import oracle
+
+    P = pts.shape[1] if max_points is None else min(max_points, pts.shape[1])
+    sub = np.ascontiguousarray(pts[:, :P])
+    threads = oracle.max_threads()
+    out = (np.zeros((system.n_polys, P, 4)), np.zeros((system.n_polys, system.n_vars, P, 4)))
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.dd_eval(system, sub, threads=threads, out=out)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return reps * P / el, threads, f"{P} points of the workload, evaluated {reps} times ({el:.1f} s)"
+
+
+def run_reference(args, rank, world):
+    """The oracle arm: the C double-double oracle on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+
+    system, pts = synth.config(CONFIG_INDEX)
+    P_step = 256  # one step = a bounded sample of the workload
+    sub = np.ascontiguousarray(pts[:, :P_step])
+    threads = oracle.max_threads()
+    out = (np.zeros((system.n_polys, P_step, 4)), np.zeros((system.n_polys, system.n_vars, P_step, 4)))
+    for _ in range(args.warmup):
+        oracle.dd_eval(system, sub, threads=threads, out=out)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.dd_eval(system, sub, threads=threads, out=out)
+    el = time.perf_counter() - t0
+    value = args.steps * P_step / el
+    sample = f"{P_step} of the 1024 points of the workload per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points_per_step": P_step, "oracle": "C double-double, term by term"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = env_dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    system, _ = synth.config(CONFIG_INDEX, n_points=1)
+    P = 1024
+    pts = synth.points(rank_points_seed(rank), system.n_vars, P)
+    n, N = system.n_vars, system.n_polys
+    ev = pkg.PolyEval(system, pkg.PE_DD, max_points=P)
+    x = torch.from_numpy(pts).to(dev)
+    f = torch.empty((N, P, 4), dtype=torch.float64, device=dev)
+    J = torch.empty((N, n, P, 4), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed_loop(evaluator, xin, fo, Jo, steps):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()  # L2 flush between timed steps (outside the step's events)
+            starts[i].record(stream)
+            evaluator.eval(xin, fo, Jo)
+            stops[i].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+
+    for _ in range(args.warmup):
+        ev.eval(x, f, J)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    pkg.polyeval_timing(ev.handle, True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    total_ms = timed_loop(ev, x, f, J, args.steps)
+    t_wall1 = time.time()
+    if dist is not None:
+        dist.barrier()
+    kern_ms, launches = pkg.polyeval_timing_read(ev.handle)
+    pkg.polyeval_timing(ev.handle, False)
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    assert ev.status() == pkg.PE_OK
+
+    ms_per_step = max_over_ranks(total_ms / args.steps, dist)
+    value = job_throughput(world, P, ms_per_step)
+
+    # roofline of the main (monomial) kernel: FP64 pipe bound
+    ops_pp, flops_pp = ev.cost()
+    kern_avg_ms = kern_ms / max(launches, 1)
+    achieved_tflops = flops_pp * P / (kern_avg_ms * 1e-3) / 1e12
+    peaks = peaks_file()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_nominal = SMS * DFMA_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
+    fma_rate, probe_mhz = pkg.polyeval_fp64_peak(stream)
+    peak_probe = 2 * fma_rate / 1e12
+    issue_rate = ops_pp * P / (kern_avg_ms * 1e-3)
+
+    # complex double path on the same workload, same harness
+    ev64 = pkg.PolyEval(system.as_fp64(), pkg.PE_F64, max_points=P)
+    x64 = torch.from_numpy(np.ascontiguousarray(pts[..., [0, 2]])).to(dev)
+    f64 = torch.empty((N, P, 2), dtype=torch.float64, device=dev)
+    J64 = torch.empty((N, n, P, 2), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        ev64.eval(x64, f64, J64)
+    k64 = max(args.steps, 10)
+    ms64 = timed_loop(ev64, x64, f64, J64, k64) / k64
+
+    # end to end through the host entry point: pinned host in, pinned host out
+    hp = torch.from_numpy(pts).pin_memory()
+    hf = torch.empty((N, P, 4), dtype=torch.float64).pin_memory()
+    hJ = torch.empty((N, n, P, 4), dtype=torch.float64).pin_memory()
+    for _ in range(max(args.warmup, 1)):
+        pkg.polyeval_eval_host(ev.handle, hp, P, hf, hJ, stream)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pkg.polyeval_eval_host(ev.handle, hp, P, hf, hJ, stream)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(system, pts, seconds=10.0)
+        cpu = {"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "evals/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_per_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points_per_gpu": P, "precision": "complex double-double",
+                       "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                       "launch": "powers kernel + persistent monomial kernel per step"},
+            "e2e": {"value": job_throughput(world, P, e2e_ms), "unit": "evals/s",
+                    "h2d_bytes_per_step": int(hp.numel() * 8), "d2h_bytes_per_step": int((hf.numel() + hJ.numel()) * 8)},
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_nominal, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak_nominal, "traffic": MAIN_KERNEL_DRAM_BYTES,
+                         "kernel": "main_kernel<ArithDD>", "kernel_ms": kern_avg_ms,
+                         "peak_basis": f"nominal: {SMS} SMs x {DFMA_PER_SM_CLK} FP64 FMA/clk x 2 flops x {sm_max:.0f} MHz",
+                         "peak_probe": peak_probe, "frac_of_probe": achieved_tflops / peak_probe,
+                         "probe_sm_mhz": probe_mhz,
+                         "fp64_issue_frac": issue_rate / (SMS * DFMA_PER_SM_CLK * sm_max * 1e6)},
+            "fp64_path": {"evals_per_s": job_throughput(world, P, ms64), "ms_per_step": ms64},
+            "dd_fp64_time_ratio": ms_per_step / ms64,
+            "fp64_peak_frac": achieved_tflops / peak_nominal,
+            "clocks": clocks,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * polyeval -- evaluation of a sparse polynomial system and its full Jacobian
+ * at many points on one GB300 GPU (sm_103a), in complex double-double or in
+ * complex double precision.
+ *
+ * The method is the one of Verschelde & Yoffe, "Evaluating polynomials in
+ * several variables and their derivatives on a GPU computing processor":
+ *   - Section 2, Eq. (1): a polynomial is a tuple (C, A) of nonzero complex
+ *     coefficients and exponent vectors; a system is a tuple of polynomials.
+ *   - Section 2 (three stages) and Section 3.1: each monomial x^a is the
+ *     common factor prod x_{i_j}^{a_j - 1} (read from a table of powers)
+ *     times the Speelpenning product x_{i_1} ... x_{i_k}.
+ *   - Section 3.2: the gradient of the Speelpenning product from forward
+ *     prefix products and one backward running product.
+ *   - Section 3.3: coefficient products and the sums into f and J.
+ *
+ * Conventions for every entry point:
+ *   - Return value: PE_OK (0) or a negative PE_E* code; nothing aborts and no
+ *     C++ exception crosses this interface.  polyeval_strerror() names codes.
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device; "host" pointers are ordinary CPU memory.
+ *   - Streams are passed as `void *` holding a cudaStream_t (NULL = legacy
+ *     default stream).  Every eval call is asynchronous on that stream.
+ *   - All sizes are element counts unless stated.
+ *
+ * Data layouts (structure of arrays, point index fastest):
+ *   - A complex double-double (pe_cdd) is 4 doubles: re_hi, re_lo, im_hi,
+ *     im_lo; the value is (re_hi + re_lo) + i (im_hi + im_lo).  A complex
+ *     double (pe_c64) is 2 doubles: re, im.
+ *   - points: [n_vars][P] entries (entry (v, q) at index v * P + q).
+ *   - out_f : [n_polys][P]          (f_p at point q at index p * P + q).
+ *   - out_J : [n_polys][n_vars][P]  (d f_p / d x_i at point q at index
+ *             (p * n_vars + i) * P + q).
+ *   Entries of J for a variable that does not occur in polynomial p are
+ *   written as exact zeros.
+ *
+ * Accuracy (normwise, against the exact result, relative to the same sum
+ * over absolute values: sum |c| |x^a| for f, sum |c| a_i |x^(a - e_i)| for
+ * J): <= 1e-28 for PE_DD and <= 1e-13 for PE_F64 on the workloads this
+ * library is tested on; see the tests for the exact cases.
+ */
+#ifndef POLYEVAL_H
+#define POLYEVAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Exported symbols of the shared library (everything else is hidden). */
+#if defined(__GNUC__)
+#define PE_API __attribute__((visibility("default")))
+#else
+#define PE_API
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PE_OK 0
+#define PE_EINVAL (-1)  /* bad argument or malformed system                  */
+#define PE_ENOMEM (-2)  /* host or device allocation failed                  */
+#define PE_ECUDA (-3)   /* a CUDA runtime call failed (see cudaGetLastError)  */
+#define PE_ERANGE (-4)  /* a size above the limits of this build             */
+#define PE_EDEVICE (-5) /* a kernel reported an inconsistency (status word)  */
+
+/* ---- precisions -------------------------------------------------------- */
+#define PE_DD 0  /* complex double-double (pe_cdd in and out)  */
+#define PE_F64 1 /* complex double        (pe_c64 in and out)  */
+
+/* ---- flags for polyeval_create / polyeval_create_many / polyeval_validate */
+#define PE_ALLOW_ZERO_COEF 1u /* accept c = 0 (Eq. 1 asks c != 0); for tests */
+
+/* ---- limits ------------------------------------------------------------ */
+#define PE_MAX_VARS 65535 /* n_vars                                        */
+#define PE_MAX_EXP 256    /* largest exponent a (the paper stores a-1 in a byte) */
+
+typedef struct {
+  double re_hi, re_lo, im_hi, im_lo;
+} pe_cdd;
+
+typedef struct {
+  double re, im;
+} pe_c64;
+
+/*
+ * A polynomial system in compressed rows (Section 2, Eq. 1; the monomial
+ * order of Section 3.3: the monomials of polynomial 0, then of polynomial 1,
+ * ...).  All arrays are host memory owned by the caller.
+ *   n_vars     number of variables n >= 1
+ *   n_polys    number of polynomials N >= 0
+ *   poly_ptr   [N + 1]   monomials of polynomial p are poly_ptr[p] ..
+ *                        poly_ptr[p+1]-1; poly_ptr[0] = 0, nondecreasing
+ *   mono_ptr   [M + 1]   (M = poly_ptr[N]) variables of monomial t are
+ *                        entries mono_ptr[t] .. mono_ptr[t+1]-1 of pos/exp;
+ *                        mono_ptr[0] = 0, nondecreasing.  k = 0 (a constant
+ *                        term) and k = 1 are allowed.
+ *   pos        variable index 0 <= pos < n, strictly increasing inside a
+ *              monomial (i_1 < i_2 < ... < i_k)
+ *   exp        exponent 1 <= a <= PE_MAX_EXP
+ *   coef       [M] coefficients, nonzero and finite.  For PE_F64 only the
+ *              high words are read.
+ */
+typedef struct {
+  int32_t n_vars;
+  int32_t n_polys;
+  const int64_t *poly_ptr;
+  const int64_t *mono_ptr;
+  const int32_t *pos;
+  const int32_t *exp;
+  const pe_cdd *coef;
+} pe_system;
+
+typedef struct polyeval polyeval_t;
+
+/*
+ * Check a system on the host only (no CUDA call).  Returns PE_OK, PE_EINVAL
+ * (null pointer, n_vars < 1, n_polys < 0, offsets not starting at 0 or
+ * decreasing, pos out of range / not strictly increasing, exponent < 1,
+ * zero or non-finite coefficient without PE_ALLOW_ZERO_COEF) or PE_ERANGE
+ * (n_vars > PE_MAX_VARS, exponent > PE_MAX_EXP, more than 2^31-1 monomials or
+ * variable entries).
+ */
+PE_API int polyeval_validate(const pe_system *sys, uint32_t flags);
+
+/*
+ * Compile one system for evaluation (Section 2 format -> device metadata).
+ *   sys         host system, copied; the caller may free it on return
+ *   precision   PE_DD or PE_F64
+ *   flags       PE_ALLOW_ZERO_COEF or 0
+ *   max_points  largest P any later polyeval_eval call will pass (>= 1);
+ *               sizes the table of powers (Section 3.1) kept on the device
+ *   out         receives the handle; *out is NULL on failure
+ * The handle owns all device memory it allocates (metadata, power table,
+ * work counter, status word); polyeval_destroy frees it.  Errors: those of
+ * polyeval_validate, PE_EINVAL for a bad precision/max_points/out,
+ * PE_ENOMEM, PE_ECUDA, PE_ERANGE when a monomial has more variables than the
+ * shared-memory prefix store of one warp can hold.
+ */
+PE_API int polyeval_create(const pe_system *sys, int precision, uint32_t flags, int64_t max_points, polyeval_t **out);
+
+/*
+ * Evaluate f and J at P points (Sections 3.1-3.3).
+ *   points  device, [n_vars][P] pe_cdd (PE_DD) or pe_c64 (PE_F64)
+ *   P       number of points, 0 <= P <= max_points (0 returns PE_OK at once)
+ *   out_f   device, [n_polys][P] of the same element type
+ *   out_J   device, [n_polys][n_vars][P] of the same element type
+ *   stream  cudaStream_t the work is queued on
+ * Allocates nothing, synchronises nothing, and only queues kernels and one
+ * 4-byte cudaMemsetAsync, so a call can be captured in a CUDA graph.  Calls
+ * on one handle must not overlap on the GPU (they share the power table and
+ * the work counter).  Errors: PE_EINVAL (null handle/pointer with P > 0),
+ * PE_ERANGE (P > max_points), PE_ECUDA (launch failure).
+ */
+PE_API int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream);
+
+/*
+ * polyeval_eval with HOST buffers: copies points to the device, evaluates,
+ * and copies f and J back, all on `stream`, then synchronises the stream.
+ * Host buffers should be pinned for full copy speed.  Device staging
+ * buffers are allocated on the first call (and grown when P grows) and kept
+ * by the handle.  Errors: as polyeval_eval, plus PE_ENOMEM.
+ */
+PE_API int polyeval_eval_host(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream);
+
+/*
+ * Compile a batch of systems of uneven shape, to be evaluated in one
+ * persistent launch (each system at its own set of points).
+ *   systems            [count] host systems (copied)
+ *   count              >= 1
+ *   points_per_system  [count] P_s >= 0 points for each system
+ * The device buffers of a batch are single arrays with every system's block
+ * at a fixed offset; polyeval_many_layout() returns the offsets.  Work items
+ * (polynomial, tile of points) are ordered by decreasing cost.  Errors: as
+ * polyeval_create.
+ */
+PE_API int polyeval_create_many(const pe_system *systems, int32_t count, int precision, uint32_t flags,
+                         const int64_t *points_per_system, polyeval_t **out);
+
+/*
+ * Offsets of system s inside the batch buffers, in elements (pe_cdd or
+ * pe_c64): its points start at points + *pt_off and are laid out
+ * [n_s][P_s]; its f at out_f + *f_off ([N_s][P_s]); its J at out_J + *J_off
+ * ([N_s][n_s][P_s]).  Any of the output pointers may be NULL.  With s = count
+ * the offsets are the total sizes.  Errors: PE_EINVAL (not a batch handle,
+ * s out of range).
+ */
+PE_API int polyeval_many_layout(const polyeval_t *h, int32_t s, int64_t *pt_off, int64_t *f_off, int64_t *J_off);
+
+/*
+ * Evaluate every system of a batch handle.  points, out_f and out_J are the
+ * device batch buffers laid out as polyeval_many_layout() describes.  Same
+ * asynchrony and graph-capture properties as polyeval_eval.
+ */
+PE_API int polyeval_eval_many(polyeval_t *h, const void *points, void *out_f, void *out_J, void *stream);
+
+/*
+ * Work counts of the handle, per evaluation point and summed over the
+ * handle's systems (for a batch: over all points of all systems, i.e. one
+ * whole polyeval_eval_many):
+ *   fp64_ops    double-precision instructions (add, mul, fma) the method
+ *               executes, counted from the compiled system
+ *   fp64_flops  the same with an fma counted as 2 flops
+ * Either pointer may be NULL.
+ */
+PE_API int polyeval_cost(const polyeval_t *h, double *fp64_ops, double *fp64_flops);
+
+/*
+ * Timing of the main (monomial) kernel, for measurement.  With enable != 0,
+ * each following eval call records a pair of CUDA events on its stream
+ * around the main kernel (at most 256 pairs are kept).  polyeval_timing_read
+ * waits for the recorded events, returns the summed kernel time in
+ * milliseconds and the number of timed launches, and starts a new count.
+ * Returns PE_ERANGE if launches beyond the 256 kept pairs went untimed.
+ */
+PE_API int polyeval_timing(polyeval_t *h, int enable);
+PE_API int polyeval_timing_read(polyeval_t *h, double *total_ms, int64_t *launches);
+
+/*
+ * Read and clear the device status word (synchronises the device).
+ * Returns PE_OK, or PE_EDEVICE if a kernel found an inconsistent index.
+ */
+PE_API int polyeval_status(polyeval_t *h);
+
+/* Free a handle and its device memory (NULL is accepted). */
+PE_API void polyeval_destroy(polyeval_t *h);
+
+/* Static string naming a status code. */
+PE_API const char *polyeval_strerror(int code);
+
+/*
+ * Measure the double-precision FMA issue rate of the current device: a
+ * short (about 2 ms) kernel of independent FMA chains on every SM, timed
+ * with CUDA events on `stream` (synchronises the stream).  *fma_per_s
+ * receives lane-FMAs per second; *sm_clock_mhz the SM clock implied by the
+ * kernel's cycle counter.  Used as the denominator of the FP64 roofline.
+ */
+PE_API int polyeval_fp64_peak(void *stream, double *fma_per_s, double *sm_clock_mhz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLYEVAL_H */

@@ -141,16 +141,26 @@ def powers_of(xv, top: int):
     return out
 
 
+class _LazyPowers:
+    """Powers [x_v^0 .. x_v^top] of each variable, made on first use."""
+
+    def __init__(self, pts, q, top):
+        self.pts, self.q, self.top, self.cache = pts, q, top, {}
+
+    def __getitem__(self, v):
+        if v not in self.cache:
+            self.cache[v] = powers_of(cx_from_dd(self.pts[v, self.q]), self.top)
+        return self.cache[v]
+
+
 def evaluate_point(system, pts, q: int, polys=None):
     """Exact f_p and row J[p, :] at point index q of ``pts`` (float64 [n, P, 4]).
 
     Returns (f, J): f[p] an exact complex; J[p] a dict {i: exact complex} of
     the variables that occur in polynomial p (absent entries are exactly 0).
     ``polys`` restricts the work to a subset of polynomial indices."""
-    n = system.n_vars
-    x = [cx_from_dd(pts[v, q]) for v in range(n)]
     top = system.max_exp
-    pw = [powers_of(x[v], top) for v in range(n)]
+    pw = _LazyPowers(pts, q, top)
     coefs = system.coef
     f, J = {}, {}
     for p in (range(system.n_polys) if polys is None else polys):
@@ -178,8 +188,9 @@ def evaluate_point(system, pts, q: int, polys=None):
 def scales_point(system, pts, q: int, polys=None):
     """Normwise scales at point q: S_f[p] = sum |c| |x|^a and
     S_J[p][i] = sum |c| a_i |x_i|^(a_i - 1) prod_{j != i} |x_j|^{a_j}, in float64."""
-    n = system.n_vars
-    ax = [math.hypot(pts[v, q, 0], pts[v, q, 2]) for v in range(n)]
+    ax = {}
+    for v in set(system.pos.tolist()):
+        ax[v] = math.hypot(pts[v, q, 0], pts[v, q, 2])
     Sf, SJ = {}, {}
     for p in (range(system.n_polys) if polys is None else polys):
         sf = 0.0

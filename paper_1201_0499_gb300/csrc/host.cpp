@@ -1,0 +1,601 @@
+// Host side of the C ABI declared in include/polyeval.h: validation of a
+// system in the format of Section 2 (Eq. 1), compilation into the device
+// layout the kernels read, work lists, launches and handle lifetime.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+#include "polyeval.h"
+
+using pe::SysDesc;
+
+namespace {
+
+constexpr int kMaxTimingEvents = 256;
+
+struct DeviceBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  ~DeviceBuf() {
+    if (p) cudaFree(p);
+  }
+  int alloc(size_t b) {
+    if (p) {
+      cudaFree(p);
+      p = nullptr;
+      bytes = 0;
+    }
+    if (b == 0) return PE_OK;
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return PE_ENOMEM;
+    }
+    bytes = b;
+    return PE_OK;
+  }
+  template <class T>
+  int upload(const std::vector<T> &v) {
+    int rc = alloc(v.size() * sizeof(T));
+    if (rc != PE_OK || v.empty()) return rc;
+    return cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess ? PE_OK : PE_ECUDA;
+  }
+};
+
+}  // namespace
+
+struct polyeval {
+  bool dd = true;
+  bool batch = false;
+  int32_t count = 0;
+  int64_t max_points = 0;
+  std::vector<SysDesc> sys;
+  int32_t n_polys_total = 0;
+  int32_t kmax = 0, kslots = 1;
+  int warps_per_block = pe::kWarpsPerBlockMax;
+  size_t smem_bytes = 0;
+  int blocks_per_sm = 1, sms = 1;
+  int blocks_per_sm_1 = 1;  // occupancy with one warp per block
+  size_t smem_per_warp = 0;
+  int64_t n_items_batch = 0;
+  int64_t power_total_batch = 0;
+  double ops_per_point = 0.0, flops_per_point = 0.0;  // single: per point; batch: per whole evaluation
+  // device memory
+  DeviceBuf poly_ptr, mono_ptr, var, coef, poly_sys, sysd, perm, items, prefix, table, counter, status;
+  DeviceBuf stage_pts, stage_f, stage_J;
+  // timing of the main kernel
+  bool timing = false;
+  cudaEvent_t ev[2 * kMaxTimingEvents] = {};
+  int ev_used = 0, ev_dropped = 0;
+  ~polyeval() {
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+int elem_doubles(const polyeval *h) { return h->dd ? 4 : 2; }
+
+// FP64 instructions and flops per point for one monomial (k variables, n2 of
+// them with exponent >= 2), as the main kernel executes them (both lanes of
+// a point).  Double-double, per lane: a product that feeds another product
+// (common factor, forward and backward chains) is a renormalised dot product,
+// 2 DMUL + 6 DFMA + 8 DADD = 16 instructions (22 flops); a final product
+// (value, derivatives) 2 DMUL + 6 DFMA + 5 DADD = 13 (19 flops); a sum 5 DADD;
+// an integer scale DMUL + 2 DFMA.  Double: a product DMUL + DFMA, a sum of J
+// one DADD, a compensated sum of f 4 DADD, a scale one DMUL.
+struct Cost {
+  double ops = 0, flops = 0;
+};
+
+Cost monomial_cost(bool dd, int k, int n2) {
+  if (k == 0) return dd ? Cost{10, 10} : Cost{8, 8};
+  const double chain = n2 + (k >= 2 ? 2.0 * k - 3.0 : 0.0);
+  const double fin = k >= 2 ? k : 1.0;
+  Cost c;
+  if (dd) {
+    c.ops = 32 * chain + 26 * fin + 10 * (k + 1) + 6 * n2;
+    c.flops = 44 * chain + 38 * fin + 10 * (k + 1) + 10 * n2;
+  } else {
+    c.ops = 4 * (chain + fin) + 2 * k + 8 + 2 * n2;
+    c.flops = 6 * (chain + fin) + 2 * k + 8 + 2 * n2;
+  }
+  return c;
+}
+
+// Per point and per polynomial: renormalising the row (double-double only)
+// and finishing f.
+Cost row_cost(bool dd, int n) { return dd ? Cost{6.0 * n + 6, 6.0 * n + 6} : Cost{2, 2}; }
+
+// Per point and per variable: the powers x^2 .. x^(emax-1).
+Cost power_cost(bool dd, int emax) {
+  const double m = emax > 2 ? emax - 2 : 0;
+  return dd ? Cost{32 * m, 44 * m} : Cost{4 * m, 6 * m};
+}
+
+int validate(const pe_system *s, uint32_t flags) {
+  if (!s || !s->poly_ptr || !s->mono_ptr) return PE_EINVAL;
+  if (s->n_vars < 1 || s->n_polys < 0) return PE_EINVAL;
+  if (s->n_vars > PE_MAX_VARS) return PE_ERANGE;
+  if (s->poly_ptr[0] != 0) return PE_EINVAL;
+  for (int32_t p = 0; p < s->n_polys; p++)
+    if (s->poly_ptr[p + 1] < s->poly_ptr[p]) return PE_EINVAL;
+  const int64_t M = s->poly_ptr[s->n_polys];
+  if (M > INT32_MAX - 1) return PE_ERANGE;
+  if (s->mono_ptr[0] != 0) return PE_EINVAL;
+  for (int64_t t = 0; t < M; t++)
+    if (s->mono_ptr[t + 1] < s->mono_ptr[t]) return PE_EINVAL;
+  const int64_t nnz = s->mono_ptr[M];
+  if (nnz > INT32_MAX - 1) return PE_ERANGE;
+  if (nnz > 0 && (!s->pos || !s->exp)) return PE_EINVAL;
+  if (M > 0 && !s->coef) return PE_EINVAL;
+  for (int64_t t = 0; t < M; t++) {
+    for (int64_t j = s->mono_ptr[t]; j < s->mono_ptr[t + 1]; j++) {
+      if (s->pos[j] < 0 || s->pos[j] >= s->n_vars) return PE_EINVAL;
+      if (j > s->mono_ptr[t] && s->pos[j] <= s->pos[j - 1]) return PE_EINVAL;
+      if (s->exp[j] < 1) return PE_EINVAL;
+      if (s->exp[j] > PE_MAX_EXP) return PE_ERANGE;
+    }
+    const pe_cdd &c = s->coef[t];
+    if (!std::isfinite(c.re_hi) || !std::isfinite(c.re_lo) || !std::isfinite(c.im_hi) || !std::isfinite(c.im_lo))
+      return PE_EINVAL;
+    const bool zero = c.re_hi == 0.0 && c.re_lo == 0.0 && c.im_hi == 0.0 && c.im_lo == 0.0;
+    if (zero && !(flags & PE_ALLOW_ZERO_COEF)) return PE_EINVAL;
+  }
+  return PE_OK;
+}
+
+struct Compiled {
+  std::vector<int32_t> poly_ptr{0}, mono_ptr{0}, poly_sys;
+  std::vector<uint32_t> var;
+  std::vector<double> coef;
+  std::vector<double> poly_ops, poly_flops;  // per point, per global polynomial
+  int32_t kmax = 0;
+};
+
+int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, SysDesc &d) {
+  d.n = s->n_vars;
+  d.N = s->n_polys;
+  d.poly0 = static_cast<int32_t>(c.poly_sys.size());
+  int32_t emax = 1;
+  const Cost rc = row_cost(dd, s->n_vars);
+  for (int32_t p = 0; p < s->n_polys; p++) {
+    Cost pc = rc;
+    for (int64_t t = s->poly_ptr[p]; t < s->poly_ptr[p + 1]; t++) {
+      const int64_t b = s->mono_ptr[t], e = s->mono_ptr[t + 1];
+      int n2 = 0;
+      for (int64_t j = b; j < e; j++) {
+        const uint32_t a = static_cast<uint32_t>(s->exp[j]);
+        c.var.push_back(static_cast<uint32_t>(s->pos[j]) | (a << 16));
+        if (a >= 2) n2++;
+        emax = std::max<int32_t>(emax, static_cast<int32_t>(a));
+      }
+      const int k = static_cast<int>(e - b);
+      c.kmax = std::max(c.kmax, k);
+      const Cost mc = monomial_cost(dd, k, n2);
+      pc.ops += mc.ops;
+      pc.flops += mc.flops;
+      if (c.var.size() > static_cast<size_t>(INT32_MAX - 1)) return PE_ERANGE;
+      c.mono_ptr.push_back(static_cast<int32_t>(c.var.size()));
+      const pe_cdd &cf = s->coef[t];
+      if (dd) {
+        c.coef.insert(c.coef.end(), {cf.re_hi, cf.re_lo, cf.im_hi, cf.im_lo});
+      } else {
+        c.coef.insert(c.coef.end(), {cf.re_hi, cf.im_hi});
+      }
+    }
+    if (c.mono_ptr.size() > static_cast<size_t>(INT32_MAX - 1)) return PE_ERANGE;
+    c.poly_ptr.push_back(static_cast<int32_t>(c.mono_ptr.size() - 1));
+    c.poly_sys.push_back(sys_index);
+    c.poly_ops.push_back(pc.ops);
+    c.poly_flops.push_back(pc.flops);
+  }
+  d.emax = emax;
+  return PE_OK;
+}
+
+int finish_handle(polyeval *h, Compiled &c) {
+  h->kmax = c.kmax;
+  h->kslots = std::max(c.kmax - 1, 1);
+  h->n_polys_total = static_cast<int32_t>(c.poly_sys.size());
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PE_ECUDA;
+  if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PE_ECUDA;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return PE_ECUDA;
+  const size_t per_warp = static_cast<size_t>(h->kslots) * 32 * (h->dd ? 16 : 8);
+  h->warps_per_block = pe::kWarpsPerBlockMax;
+  while (h->warps_per_block > 1 && per_warp * h->warps_per_block > static_cast<size_t>(optin)) h->warps_per_block /= 2;
+  if (per_warp * h->warps_per_block > static_cast<size_t>(optin)) return PE_ERANGE;
+  h->smem_bytes = per_warp * h->warps_per_block;
+  h->smem_per_warp = per_warp;
+  if (pe::prepare_main(h->dd, static_cast<size_t>(optin)) != cudaSuccess) return PE_ECUDA;
+  if (pe::main_occupancy(h->dd, h->warps_per_block, h->smem_bytes, &h->blocks_per_sm) != cudaSuccess) return PE_ECUDA;
+  if (pe::main_occupancy(h->dd, 1, per_warp, &h->blocks_per_sm_1) != cudaSuccess) return PE_ECUDA;
+  if (h->blocks_per_sm < 1 || h->blocks_per_sm_1 < 1) return PE_ERANGE;
+  int rc;
+  if ((rc = h->poly_ptr.upload(c.poly_ptr)) || (rc = h->mono_ptr.upload(c.mono_ptr)) || (rc = h->var.upload(c.var)) ||
+      (rc = h->coef.upload(c.coef)) || (rc = h->poly_sys.upload(c.poly_sys)) || (rc = h->sysd.upload(h->sys)))
+    return rc;
+  if ((rc = h->counter.alloc(sizeof(unsigned))) || (rc = h->status.alloc(sizeof(int)))) return rc;
+  if (cudaMemset(h->status.p, 0, sizeof(int)) != cudaSuccess) return PE_ECUDA;
+  return PE_OK;
+}
+
+// Launch shape.  When every item fits in one wave of resident warps, launch
+// one single-warp block per item: the block scheduler then spreads the warps
+// over the SMs to within one warp, which balances the FP64 pipe of every SM.
+// Otherwise a persistent grid of full blocks takes items from the counter.
+struct Shape {
+  int grid, warps;
+  size_t smem;
+};
+
+Shape shape_for(const polyeval *h, int64_t n_items) {
+  if (n_items <= static_cast<int64_t>(h->sms) * h->blocks_per_sm_1)
+    return Shape{static_cast<int>(std::max<int64_t>(1, n_items)), 1, h->smem_per_warp};
+  const int64_t full = static_cast<int64_t>(h->sms) * h->blocks_per_sm;
+  const int64_t need = (n_items + h->warps_per_block - 1) / h->warps_per_block;
+  return Shape{static_cast<int>(std::max<int64_t>(1, std::min(full, need))), h->warps_per_block, h->smem_bytes};
+}
+
+pe::MainParams main_params(const polyeval *h) {
+  pe::MainParams p{};
+  p.poly_ptr = static_cast<const int32_t *>(h->poly_ptr.p);
+  p.mono_ptr = static_cast<const int32_t *>(h->mono_ptr.p);
+  p.var = static_cast<const uint32_t *>(h->var.p);
+  p.coef = static_cast<const double *>(h->coef.p);
+  p.poly_sys = static_cast<const int32_t *>(h->poly_sys.p);
+  p.sys = static_cast<const SysDesc *>(h->sysd.p);
+  p.perm = static_cast<const int32_t *>(h->perm.p);
+  p.items = static_cast<const int2 *>(h->items.p);
+  p.table = static_cast<const double *>(h->table.p);
+  p.kslots = h->kslots;
+  p.n_polys_total = h->n_polys_total;
+  p.counter = static_cast<unsigned *>(h->counter.p);
+  p.status = static_cast<int *>(h->status.p);
+  return p;
+}
+
+int run_main(polyeval *h, const pe::MainParams &mp, cudaStream_t s) {
+  if (mp.n_items <= 0) return PE_OK;
+  if (cudaMemsetAsync(h->counter.p, 0, sizeof(unsigned), s) != cudaSuccess) return PE_ECUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->timing) {
+    if (h->ev_used < kMaxTimingEvents) {
+      e0 = h->ev[2 * h->ev_used];
+      e1 = h->ev[2 * h->ev_used + 1];
+      h->ev_used++;
+    } else {
+      h->ev_dropped++;
+    }
+  }
+  if (e0 && cudaEventRecord(e0, s) != cudaSuccess) return PE_ECUDA;
+  const Shape sh = shape_for(h, mp.n_items);
+  if (pe::launch_main(h->dd, mp, sh.warps, sh.smem, sh.grid, s) != cudaSuccess) return PE_ECUDA;
+  if (e1 && cudaEventRecord(e1, s) != cudaSuccess) return PE_ECUDA;
+  return PE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int polyeval_validate(const pe_system *sys, uint32_t flags) { return validate(sys, flags); }
+
+int polyeval_create(const pe_system *sys, int precision, uint32_t flags, int64_t max_points, polyeval_t **out) {
+  if (!out) return PE_EINVAL;
+  *out = nullptr;
+  if (precision != PE_DD && precision != PE_F64) return PE_EINVAL;
+  if (max_points < 1) return PE_EINVAL;
+  int rc = validate(sys, flags);
+  if (rc != PE_OK) return rc;
+  polyeval *h = nullptr;
+  try {
+    h = new polyeval();
+    h->dd = precision == PE_DD;
+    h->batch = false;
+    h->count = 1;
+    h->max_points = max_points;
+    h->sys.resize(1);
+    Compiled c;
+    if ((rc = append_system(c, sys, 0, h->dd, h->sys[0])) != PE_OK) {
+      delete h;
+      return rc;
+    }
+    SysDesc &d = h->sys[0];
+    const int64_t tiles = (max_points + pe::kPointsPerWarp - 1) / pe::kPointsPerWarp;
+    if (static_cast<int64_t>(d.N) * tiles > INT32_MAX || max_points > INT32_MAX) {
+      delete h;
+      return PE_ERANGE;
+    }
+    d.P = 0;
+    d.tiles = 0;
+    d.pt_off = d.f_off = d.J_off = d.tab_off = 0;
+    // polynomials by decreasing cost (largest first), stable
+    std::vector<int32_t> perm(d.N);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return c.poly_ops[a] > c.poly_ops[b]; });
+    double ops = 0, flops = 0;
+    for (int32_t p = 0; p < d.N; p++) {
+      ops += c.poly_ops[p];
+      flops += c.poly_flops[p];
+    }
+    const Cost pw = power_cost(h->dd, d.emax);
+    h->ops_per_point = ops + pw.ops * d.n;
+    h->flops_per_point = flops + pw.flops * d.n;
+    if ((rc = finish_handle(h, c)) != PE_OK || (rc = h->perm.upload(perm)) != PE_OK) {
+      delete h;
+      return rc;
+    }
+    if (d.emax > 2) {
+      const size_t entries = static_cast<size_t>(d.emax - 2) * d.n * static_cast<size_t>(max_points);
+      if ((rc = h->table.alloc(entries * elem_doubles(h) * sizeof(double))) != PE_OK) {
+        delete h;
+        return rc;
+      }
+    }
+  } catch (const std::bad_alloc &) {
+    delete h;
+    return PE_ENOMEM;
+  }
+  *out = h;
+  return PE_OK;
+}
+
+int polyeval_create_many(const pe_system *systems, int32_t count, int precision, uint32_t flags,
+                         const int64_t *points_per_system, polyeval_t **out) {
+  if (!out) return PE_EINVAL;
+  *out = nullptr;
+  if (!systems || !points_per_system || count < 1) return PE_EINVAL;
+  if (precision != PE_DD && precision != PE_F64) return PE_EINVAL;
+  for (int32_t s = 0; s < count; s++) {
+    int rc = validate(&systems[s], flags);
+    if (rc != PE_OK) return rc;
+    if (points_per_system[s] < 0 || points_per_system[s] > INT32_MAX) return PE_EINVAL;
+  }
+  polyeval *h = nullptr;
+  int rc = PE_OK;
+  try {
+    h = new polyeval();
+    h->dd = precision == PE_DD;
+    h->batch = true;
+    h->count = count;
+    h->sys.resize(count);
+    Compiled c;
+    int64_t pt = 0, fo = 0, jo = 0, to = 0;
+    std::vector<int64_t> prefix{0};
+    struct Item {
+      int32_t gp, tile;
+      double cost;
+    };
+    std::vector<Item> items;
+    double ops = 0, flops = 0;
+    for (int32_t s = 0; s < count; s++) {
+      SysDesc &d = h->sys[s];
+      if ((rc = append_system(c, &systems[s], s, h->dd, d)) != PE_OK) {
+        delete h;
+        return rc;
+      }
+      const int64_t P = points_per_system[s];
+      d.P = static_cast<int32_t>(P);
+      d.tiles = static_cast<int32_t>((P + pe::kPointsPerWarp - 1) / pe::kPointsPerWarp);
+      d.pt_off = pt;
+      d.f_off = fo;
+      d.J_off = jo;
+      d.tab_off = to;
+      pt += static_cast<int64_t>(d.n) * P;
+      fo += static_cast<int64_t>(d.N) * P;
+      jo += static_cast<int64_t>(d.N) * d.n * P;
+      const bool tab = d.emax > 2 && P > 0;
+      to += tab ? static_cast<int64_t>(d.emax - 2) * d.n * P : 0;
+      prefix.push_back(prefix.back() + (tab ? static_cast<int64_t>(d.n) * P : 0));
+      const Cost pw = power_cost(h->dd, d.emax);
+      ops += pw.ops * d.n * P;
+      flops += pw.flops * d.n * P;
+      for (int32_t p = 0; p < d.N; p++) {
+        const int32_t gp = d.poly0 + p;
+        ops += c.poly_ops[gp] * P;
+        flops += c.poly_flops[gp] * P;
+        for (int32_t tl = 0; tl < d.tiles; tl++) {
+          const int32_t in_tile = static_cast<int32_t>(std::min<int64_t>(pe::kPointsPerWarp, P - tl * pe::kPointsPerWarp));
+          items.push_back(Item{gp, tl, c.poly_ops[gp] * in_tile});
+        }
+      }
+    }
+    if (items.size() > static_cast<size_t>(INT32_MAX)) {
+      delete h;
+      return PE_ERANGE;
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
+    std::vector<int32_t> it2;
+    it2.reserve(items.size() * 2);
+    for (const Item &it : items) {
+      it2.push_back(it.gp);
+      it2.push_back(it.tile);
+    }
+    h->n_items_batch = static_cast<int64_t>(items.size());
+    h->power_total_batch = prefix.back();
+    h->ops_per_point = ops;
+    h->flops_per_point = flops;
+    if ((rc = finish_handle(h, c)) != PE_OK || (rc = h->items.upload(it2)) != PE_OK ||
+        (rc = h->prefix.upload(prefix)) != PE_OK || (rc = h->table.alloc(static_cast<size_t>(to) * elem_doubles(h) *
+                                                                          sizeof(double))) != PE_OK) {
+      delete h;
+      return rc;
+    }
+  } catch (const std::bad_alloc &) {
+    delete h;
+    return PE_ENOMEM;
+  }
+  *out = h;
+  return PE_OK;
+}
+
+int polyeval_many_layout(const polyeval_t *h, int32_t s, int64_t *pt_off, int64_t *f_off, int64_t *J_off) {
+  if (!h || !h->batch || s < 0 || s > h->count) return PE_EINVAL;
+  int64_t a, b, c;
+  if (s < h->count) {
+    a = h->sys[s].pt_off;
+    b = h->sys[s].f_off;
+    c = h->sys[s].J_off;
+  } else {
+    const SysDesc &d = h->sys[h->count - 1];
+    a = d.pt_off + static_cast<int64_t>(d.n) * d.P;
+    b = d.f_off + static_cast<int64_t>(d.N) * d.P;
+    c = d.J_off + static_cast<int64_t>(d.N) * d.n * d.P;
+  }
+  if (pt_off) *pt_off = a;
+  if (f_off) *f_off = b;
+  if (J_off) *J_off = c;
+  return PE_OK;
+}
+
+int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream) {
+  if (!h || h->batch || P < 0) return PE_EINVAL;
+  if (P == 0) return PE_OK;
+  if (P > h->max_points) return PE_ERANGE;
+  if (!points || (!out_f && h->sys[0].N > 0) || (!out_J && h->sys[0].N > 0)) return PE_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const SysDesc &d = h->sys[0];
+  if (d.emax > 2) {
+    pe::PowerParams pp{};
+    pp.sys = static_cast<const SysDesc *>(h->sysd.p);
+    pp.points = static_cast<const double *>(points);
+    pp.table = static_cast<double *>(h->table.p);
+    pp.total = static_cast<int64_t>(d.n) * P;
+    pp.count = 1;
+    pp.single_P = static_cast<int32_t>(P);
+    pp.single_n = d.n;
+    pp.single_emax = d.emax;
+    if (pe::launch_powers(h->dd, pp, s) != cudaSuccess) return PE_ECUDA;
+  }
+  pe::MainParams mp = main_params(h);
+  mp.points = static_cast<const double *>(points);
+  mp.out_f = static_cast<double *>(out_f);
+  mp.out_J = static_cast<double *>(out_J);
+  mp.single_P = static_cast<int32_t>(P);
+  mp.single_T = static_cast<int32_t>((P + pe::kPointsPerWarp - 1) / pe::kPointsPerWarp);
+  mp.n_items = static_cast<int64_t>(d.N) * mp.single_T;
+  return run_main(h, mp, s);
+}
+
+int polyeval_eval_many(polyeval_t *h, const void *points, void *out_f, void *out_J, void *stream) {
+  if (!h || !h->batch) return PE_EINVAL;
+  if (h->n_items_batch == 0) return PE_OK;
+  if (!points || !out_f || !out_J) return PE_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->power_total_batch > 0) {
+    pe::PowerParams pp{};
+    pp.sys = static_cast<const SysDesc *>(h->sysd.p);
+    pp.prefix = static_cast<const int64_t *>(h->prefix.p);
+    pp.points = static_cast<const double *>(points);
+    pp.table = static_cast<double *>(h->table.p);
+    pp.total = h->power_total_batch;
+    pp.count = h->count;
+    pp.single_P = -1;
+    if (pe::launch_powers(h->dd, pp, s) != cudaSuccess) return PE_ECUDA;
+  }
+  pe::MainParams mp = main_params(h);
+  mp.points = static_cast<const double *>(points);
+  mp.out_f = static_cast<double *>(out_f);
+  mp.out_J = static_cast<double *>(out_J);
+  mp.single_P = -1;
+  mp.single_T = 0;
+  mp.n_items = h->n_items_batch;
+  return run_main(h, mp, s);
+}
+
+int polyeval_eval_host(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream) {
+  if (!h || h->batch || P < 0) return PE_EINVAL;
+  if (P == 0) return PE_OK;
+  if (P > h->max_points) return PE_ERANGE;
+  if (!points || !out_f || !out_J) return PE_EINVAL;
+  const SysDesc &d = h->sys[0];
+  const size_t eb = static_cast<size_t>(elem_doubles(h)) * sizeof(double);
+  const size_t bp = eb * d.n * static_cast<size_t>(P), bf = eb * d.N * static_cast<size_t>(P),
+               bj = eb * d.N * static_cast<size_t>(d.n) * static_cast<size_t>(P);
+  int rc;
+  if (h->stage_pts.bytes < bp && (rc = h->stage_pts.alloc(bp)) != PE_OK) return rc;
+  if (h->stage_f.bytes < bf && (rc = h->stage_f.alloc(bf)) != PE_OK) return rc;
+  if (h->stage_J.bytes < bj && (rc = h->stage_J.alloc(bj)) != PE_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(h->stage_pts.p, points, bp, cudaMemcpyHostToDevice, s) != cudaSuccess) return PE_ECUDA;
+  if ((rc = polyeval_eval(h, h->stage_pts.p, P, h->stage_f.p, h->stage_J.p, stream)) != PE_OK) return rc;
+  if (bf && cudaMemcpyAsync(out_f, h->stage_f.p, bf, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PE_ECUDA;
+  if (bj && cudaMemcpyAsync(out_J, h->stage_J.p, bj, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PE_ECUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? PE_OK : PE_ECUDA;
+}
+
+int polyeval_cost(const polyeval_t *h, double *fp64_ops, double *fp64_flops) {
+  if (!h) return PE_EINVAL;
+  if (fp64_ops) *fp64_ops = h->ops_per_point;
+  if (fp64_flops) *fp64_flops = h->flops_per_point;
+  return PE_OK;
+}
+
+int polyeval_timing(polyeval_t *h, int enable) {
+  if (!h) return PE_EINVAL;
+  if (enable && !h->ev[0]) {
+    for (auto &e : h->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return PE_ECUDA;
+  }
+  h->timing = enable != 0;
+  h->ev_used = 0;
+  h->ev_dropped = 0;
+  return PE_OK;
+}
+
+int polyeval_timing_read(polyeval_t *h, double *total_ms, int64_t *launches) {
+  if (!h) return PE_EINVAL;
+  double tot = 0.0;
+  for (int i = 0; i < h->ev_used; i++) {
+    if (cudaEventSynchronize(h->ev[2 * i + 1]) != cudaSuccess) return PE_ECUDA;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]) != cudaSuccess) return PE_ECUDA;
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = h->ev_used;
+  const int dropped = h->ev_dropped;
+  h->ev_used = 0;
+  h->ev_dropped = 0;
+  return dropped ? PE_ERANGE : PE_OK;
+}
+
+int polyeval_status(polyeval_t *h) {
+  if (!h) return PE_EINVAL;
+  int v = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return PE_ECUDA;
+  if (cudaMemcpy(&v, h->status.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PE_ECUDA;
+  if (cudaMemset(h->status.p, 0, sizeof(int)) != cudaSuccess) return PE_ECUDA;
+  return v ? PE_EDEVICE : PE_OK;
+}
+
+void polyeval_destroy(polyeval_t *h) { delete h; }
+
+const char *polyeval_strerror(int code) {
+  switch (code) {
+    case PE_OK: return "ok";
+    case PE_EINVAL: return "invalid argument or malformed system";
+    case PE_ENOMEM: return "out of memory";
+    case PE_ECUDA: return "CUDA runtime error";
+    case PE_ERANGE: return "size beyond the limits of this build";
+    case PE_EDEVICE: return "a kernel reported an inconsistent index";
+    default: return "unknown status code";
+  }
+}
+
+int polyeval_fp64_peak(void *stream, double *fma_per_s, double *sm_clock_mhz) {
+  return pe::fp64_peak_probe(static_cast<cudaStream_t>(stream), fma_per_s, sm_clock_mhz) == cudaSuccess ? PE_OK
+                                                                                                        : PE_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// Internal interface between the host side (host.cpp) and the kernels
+// (kernels.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pe {
+
+// Points handled by one warp: two lanes per point, lane 2q holds the real
+// part and lane 2q+1 the imaginary part of every value of point q.
+constexpr int kPointsPerWarp = 16;
+constexpr int kWarpsPerBlockMax = 4;
+
+// One compiled system inside a handle.  Offsets are in complex elements of
+// the handle's precision.
+struct SysDesc {
+  int32_t n;       // variables
+  int32_t N;       // polynomials
+  int32_t emax;    // largest exponent
+  int32_t P;       // points (batch handles; single handles pass P per call)
+  int32_t poly0;   // first global polynomial index
+  int32_t tiles;   // ceil(P / kPointsPerWarp) (batch handles)
+  int64_t pt_off;  // points  [n][P]
+  int64_t f_off;   // f       [N][P]
+  int64_t J_off;   // J       [N][n][P]
+  int64_t tab_off; // powers  [emax-2][n][P]  (x^2 .. x^(emax-1))
+};
+
+struct MainParams {
+  const int32_t *poly_ptr;  // [Ntot+1] global monomial offsets
+  const int32_t *mono_ptr;  // [Mtot+1] offsets into var
+  const uint32_t *var;      // [nnz] position | exponent << 16
+  const double *coef;       // [Mtot] complex coefficients (4 or 2 doubles)
+  const int32_t *poly_sys;  // [Ntot] system of each global polynomial
+  const SysDesc *sys;       // [count]
+  const int32_t *perm;      // single handle: polynomials by decreasing cost
+  const int2 *items;        // batch handle: (global polynomial, tile) by decreasing cost
+  const double *points;
+  double *out_f;
+  double *out_J;
+  const double *table;
+  int64_t n_items;
+  int32_t single_P;         // >= 0: single-system handle evaluated at single_P points
+  int32_t single_T;         // tiles of a single-system call
+  int32_t kslots;           // prefix-product slots per lane (max k - 1, at least 1)
+  int32_t n_polys_total;
+  unsigned int *counter;    // work counter (zeroed before each launch)
+  int *status;              // device status word
+};
+
+struct PowerParams {
+  const SysDesc *sys;
+  const int64_t *prefix;    // batch: [count+1] prefix sums of n_s * P_s over systems with emax > 2
+  const double *points;
+  double *table;
+  int64_t total;            // number of (system, variable, point) entries
+  int32_t count;
+  int32_t single_P;         // >= 0: single-system handle
+  int32_t single_n;
+  int32_t single_emax;
+};
+
+// Launchers (kernels.cu).  `dd` selects complex double-double, else complex
+// double.  They return the cudaError_t of the launch.
+cudaError_t launch_powers(bool dd, const PowerParams &p, cudaStream_t s);
+cudaError_t launch_main(bool dd, const MainParams &p, int warps_per_block, size_t smem_bytes, int grid,
+                        cudaStream_t s);
+cudaError_t main_occupancy(bool dd, int warps_per_block, size_t smem_bytes, int *blocks_per_sm);
+cudaError_t prepare_main(bool dd, size_t smem_bytes);
+cudaError_t fp64_peak_probe(cudaStream_t s, double *fma_per_s, double *sm_clock_mhz);
+
+}  // namespace pe

@@ -1,0 +1,424 @@
+// Kernels for the evaluation of a sparse polynomial system and its Jacobian
+// (Verschelde & Yoffe, Sections 3.1-3.3), written for sm_103a.
+//
+// GB300 design (the paper's Tesla C2050 three-kernel design is prior art):
+//
+//  * The FP64 pipe is the bound: every value is a complex double-double (or
+//    a complex double) and a double-precision instruction costs a warp 16 SM
+//    cycles, so the kernels are laid out to issue as few of them as possible
+//    and to keep at least one warp on every SM sub-partition.
+//  * One warp evaluates one polynomial p of one system at a tile of 16
+//    points.  Lanes 2q and 2q+1 hold the real and the imaginary part of every
+//    value of point q, so a complex product is one double-double dot product
+//    of length two per lane (13 FP64 instructions) plus shuffles with the
+//    partner lane.  Every lane of the warp works on the same monomial: the
+//    positions, exponents and coefficients are warp-uniform loads and
+//    monomials of different k cause no divergence.
+//  * Stage 1 (Section 3.1): the powers x_i^2 .. x_i^(d-1) are computed once
+//    per point by a small kernel into a table in global memory (L2
+//    resident); the common factor of a monomial is read from it.  The
+//    coefficient is folded into the common factor, G = c prod x^(a-1).
+//  * Stage 2 (Section 3.2): the forward products G x_{i_1} ... x_{i_j} are
+//    kept in shared memory (one slot per variable per lane) and the backward
+//    product Q in registers; d/dx_{i_j} of the term is a_j G prod_{l != j}
+//    x_{i_l}.  A monomial with k variables costs #(a >= 2) + 3k - 3 complex
+//    products instead of the paper's 6k - 5.
+//  * Stage 3 (Section 3.3): the warp adds its terms straight into f (in
+//    registers) and into the row J[p, :] of its points (read-modify-write in
+//    the output array, which only this warp touches).  Only the nm(k+1) real
+//    terms are added -- no zero padding -- in a fixed order, so results are
+//    deterministic.  The row is renormalised once at the end.
+//  * Work distribution: a persistent grid; each warp takes (polynomial,
+//    tile) items from an atomic counter, most expensive first.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dd.cuh"
+#include "internal.h"
+
+namespace pe {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kSign = 0x8000000000000000ULL;
+
+// ---------------------------------------------------------------------------
+// precision policies: one real component per lane
+// ---------------------------------------------------------------------------
+
+struct ArithDD {
+  using V = dd;         // one component (real or imaginary) held by a lane
+  using F = dd;         // accumulator of f
+  static constexpr int kDoubles = 4;  // doubles per complex element
+  struct Full {
+    dd re, im;
+  };
+
+  __device__ static Full load_full(const double *p) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return Full{dd{a.x, a.y}, dd{b.x, b.y}};
+  }
+  __device__ static void store_full(double *p, const Full &x) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(x.re.h, x.re.l);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(x.im.h, x.im.l);
+  }
+  __device__ static Full load_coherent(const double *p) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    const double2 b = reinterpret_cast<const double2 *>(p)[1];
+    return Full{dd{a.x, a.y}, dd{b.x, b.y}};
+  }
+  __device__ static V load_comp_ro(const double *p, int c) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p) + c);
+    return dd{a.x, a.y};
+  }
+  __device__ static V load_comp(const double *p, int c) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[c];
+    return dd{a.x, a.y};
+  }
+  __device__ static void store_comp(double *p, int c, V v) {
+    reinterpret_cast<double2 *>(p)[c] = make_double2(v.h, v.l);
+  }
+  __device__ static V zero() { return dd{0.0, 0.0}; }
+  __device__ static V comp(const Full &x, int c) { return select(c == 0, x.re, x.im); }
+  __device__ static V im_signed(const Full &x, unsigned long long m) { return negate_if(x.im, m); }
+  __device__ static V neg_if(V x, unsigned long long m) { return negate_if(x, m); }
+  __device__ static V sel(bool t, V a, V b) { return select(t, a, b); }
+  __device__ static V partner(V x) { return shfl_xor(x, 1); }
+  __device__ static V dot(V a1, V b1, V a2, V b2) { return dot2(a1, b1, a2, b2); }
+  __device__ static V dotn(V a1, V b1, V a2, V b2) { return dot2n(a1, b1, a2, b2); }
+  __device__ static V add(V a, V b) { return pe::add(a, b); }
+  __device__ static V mul_int(V x, double k) { return scale(x, k); }
+  __device__ static V finish(V x) { return normalize(x); }
+  __device__ static F f_zero() { return dd{0.0, 0.0}; }
+  __device__ static F f_add(F a, V x) { return pe::add(a, x); }
+  __device__ static V f_finish(F a) { return normalize(a); }
+  __device__ static Full cmul(const Full &x, const Full &y) {
+    return Full{dot2n(x.re, y.re, negate_if(x.im, kSign), y.im), dot2n(x.re, y.im, x.im, y.re)};
+  }
+};
+
+struct ArithF64 {
+  using V = double;
+  using F = dd;  // compensated sum of f: (running sum, sum of rounding errors)
+  static constexpr int kDoubles = 2;
+  struct Full {
+    double re, im;
+  };
+
+  __device__ static Full load_full(const double *p) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    return Full{a.x, a.y};
+  }
+  __device__ static void store_full(double *p, const Full &x) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(x.re, x.im);
+  }
+  __device__ static Full load_coherent(const double *p) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    return Full{a.x, a.y};
+  }
+  __device__ static V load_comp_ro(const double *p, int c) { return __ldg(p + c); }
+  __device__ static V load_comp(const double *p, int c) { return p[c]; }
+  __device__ static void store_comp(double *p, int c, V v) { p[c] = v; }
+  __device__ static V zero() { return 0.0; }
+  __device__ static V comp(const Full &x, int c) { return select(c == 0, x.re, x.im); }
+  __device__ static V im_signed(const Full &x, unsigned long long m) { return negate_if(x.im, m); }
+  __device__ static V neg_if(V x, unsigned long long m) { return negate_if(x, m); }
+  __device__ static V sel(bool t, V a, V b) { return select(t, a, b); }
+  __device__ static V partner(V x) { return shfl_xor(x, 1); }
+  __device__ static V dot(V a1, V b1, V a2, V b2) { return __fma_rn(a1, b1, __dmul_rn(a2, b2)); }
+  __device__ static V dotn(V a1, V b1, V a2, V b2) { return dot(a1, b1, a2, b2); }
+  __device__ static V add(V a, V b) { return __dadd_rn(a, b); }
+  __device__ static V mul_int(V x, double k) { return __dmul_rn(x, k); }
+  __device__ static V finish(V x) { return x; }
+  __device__ static F f_zero() { return dd{0.0, 0.0}; }
+  __device__ static F f_add(F a, V x) {
+    double s, e;
+    two_sum(a.h, x, s, e);
+    return dd{s, __dadd_rn(a.l, e)};
+  }
+  __device__ static V f_finish(F a) { return __dadd_rn(a.h, a.l); }
+  __device__ static Full cmul(const Full &x, const Full &y) {
+    return Full{__fma_rn(x.re, y.re, -__dmul_rn(x.im, y.im)), __fma_rn(x.re, y.im, __dmul_rn(x.im, y.re))};
+  }
+};
+
+// y * X for y split across the lane pair (this lane holds component c) and X
+// a full complex value loaded by both lanes:
+//   re: X.re y.re - X.im y.im     im: X.re y.im + X.im y.re
+// i.e. X.re * y_own + (sign * X.im) * y_partner with sign -1 on real lanes.
+// Norm: renormalise the result (for a product that feeds another product).
+template <class A, bool Norm>
+__device__ __forceinline__ typename A::V mul_x(typename A::V y, const typename A::Full &X, unsigned long long sgn) {
+  const typename A::V yp = A::partner(y);
+  return Norm ? A::dotn(X.re, y, A::im_signed(X, sgn), yp) : A::dot(X.re, y, A::im_signed(X, sgn), yp);
+}
+
+// P * Q with both factors split across the lane pair:
+//   re lane: P.re Q.re - P.im Q.im      im lane: P.im Q.re + P.re Q.im
+template <class A>
+__device__ __forceinline__ typename A::V mul_split(typename A::V P, typename A::V Q, int c, unsigned long long sgn) {
+  const typename A::V Pp = A::partner(P);
+  const typename A::V Qp = A::partner(Q);
+  const bool re = (c == 0);
+  return A::dot(P, A::sel(re, Q, Qp), A::neg_if(Pp, sgn), A::sel(re, Qp, Q));
+}
+
+template <class A>
+__device__ __forceinline__ void accumulate(double *p, int c, bool valid, typename A::V d) {
+  const typename A::V acc = A::add(A::load_comp(p, c), d);
+  if (valid) A::store_comp(p, c, acc);
+}
+
+// One work item: polynomial gp (global index) of system s at the points of
+// `tile`.  smem: this warp's prefix-product slots, [slot][lane].
+template <class A>
+__device__ void process_item(const MainParams &kp, int gp, int tile, int s, int P, typename A::V *smem, int lane) {
+  using V = typename A::V;
+  using Full = typename A::Full;
+  constexpr int KD = A::kDoubles;
+  const SysDesc sd = kp.sys[s];
+  const int n = sd.n;
+  const int q = tile * kPointsPerWarp + (lane >> 1);
+  const bool valid = q < P;
+  const int qc = valid ? q : P - 1;  // lanes past the end compute on the last point and store nothing
+  const int c = lane & 1;
+  const unsigned long long sgn = c ? 0ULL : kSign;
+  const size_t Pz = static_cast<size_t>(P);
+  const int pl = gp - sd.poly0;
+  const double *X = kp.points + static_cast<size_t>(sd.pt_off) * KD;
+  const double *Tb = kp.table + static_cast<size_t>(sd.tab_off) * KD;
+  double *Jrow = kp.out_J + (static_cast<size_t>(sd.J_off) + static_cast<size_t>(pl) * n * Pz) * KD;
+
+  auto xel = [&](int v) { return X + (static_cast<size_t>(v) * Pz + qc) * KD; };
+  auto tel = [&](int e, int v) { return Tb + ((static_cast<size_t>(e - 2) * n + v) * Pz + qc) * KD; };
+  auto jel = [&](int v) { return Jrow + (static_cast<size_t>(v) * Pz + qc) * KD; };
+
+  if (valid)
+    for (int v = 0; v < n; v++) A::store_comp(jel(v), c, A::zero());
+
+  typename A::F f = A::f_zero();
+  const int t0 = kp.poly_ptr[gp], t1 = kp.poly_ptr[gp + 1];
+  for (int t = t0; t < t1; t++) {
+    const int vb = kp.mono_ptr[t];
+    const int k = kp.mono_ptr[t + 1] - vb;
+    V G = A::load_comp_ro(kp.coef + static_cast<size_t>(t) * KD, c);
+    if (k == 0) {  // constant term
+      f = A::f_add(f, G);
+      continue;
+    }
+    const uint32_t *vw = kp.var + vb;
+    // Stage 1: G = c * prod_{a_j >= 2} x_{i_j}^(a_j - 1)
+    for (int j = 0; j < k; j++) {
+      const uint32_t w = __ldg(vw + j);
+      const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
+      if (a >= 2) G = mul_x<A, true>(G, A::load_full(a == 2 ? xel(v) : tel(a - 1, v)), sgn);
+    }
+    // Stage 2, forward: slot j <- G x_{i_1} ... x_{i_j}, j = 0 .. k-2
+    V Pc = G;
+    for (int j = 0; j < k - 1; j++) {
+      smem[j * 32 + lane] = Pc;
+      const int v = static_cast<int>(__ldg(vw + j) & 0xffffu);
+      Pc = mul_x<A, true>(Pc, A::load_full(xel(v)), sgn);
+    }
+    // value c x^a = Pc x_{i_k}; derivative by x_{i_k} = a_k Pc
+    const uint32_t wl = __ldg(vw + k - 1);
+    const int vl = static_cast<int>(wl & 0xffffu), al = static_cast<int>(wl >> 16);
+    const Full xl = A::load_full(xel(vl));
+    f = A::f_add(f, mul_x<A, false>(Pc, xl, sgn));
+    accumulate<A>(jel(vl), c, valid, al == 1 ? Pc : A::mul_int(Pc, static_cast<double>(al)));
+    // Stage 2, backward: Q = x_{i_{j+2}} ... x_{i_k}; derivative by x_{i_{j+1}} = a_{j+1} slot_j Q
+    V Q = A::comp(xl, c);
+    for (int j = k - 2; j >= 0; j--) {
+      const uint32_t w = __ldg(vw + j);
+      const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
+      const V D = mul_split<A>(smem[j * 32 + lane], Q, c, sgn);
+      accumulate<A>(jel(v), c, valid, a == 1 ? D : A::mul_int(D, static_cast<double>(a)));
+      if (j > 0) Q = mul_x<A, true>(Q, A::load_full(xel(v)), sgn);
+    }
+  }
+  if (valid) {
+    A::store_comp(kp.out_f + (static_cast<size_t>(sd.f_off) + static_cast<size_t>(pl) * Pz + q) * KD, c,
+                  A::f_finish(f));
+    for (int v = 0; v < n; v++) {
+      double *p = jel(v);
+      A::store_comp(p, c, A::finish(A::load_comp(p, c)));
+    }
+  }
+}
+
+template <class A>
+__global__ void __launch_bounds__(kWarpsPerBlockMax * 32) main_kernel(const MainParams kp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  typename A::V *smem = reinterpret_cast<typename A::V *>(smem_raw) + static_cast<size_t>(warp) * kp.kslots * 32;
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(kp.counter, 1u);
+    item = __shfl_sync(kFull, item, 0);
+    if (static_cast<int64_t>(item) >= kp.n_items) break;
+    int gp, tile, s, P;
+    if (kp.single_P >= 0) {
+      const int r = static_cast<int>(item) / kp.single_T;
+      tile = static_cast<int>(item) - r * kp.single_T;
+      gp = kp.perm[r];
+      s = 0;
+      P = kp.single_P;
+    } else {
+      const int2 it = kp.items[item];
+      gp = it.x;
+      tile = it.y;
+      s = (gp >= 0 && gp < kp.n_polys_total) ? kp.poly_sys[gp] : 0;
+      P = kp.sys[s].P;
+    }
+    if (gp < 0 || gp >= kp.n_polys_total || tile * kPointsPerWarp >= P) {
+      if (lane == 0) atomicOr(kp.status, 1);
+      continue;
+    }
+    process_item<A>(kp, gp, tile, s, P, smem, lane);
+  }
+}
+
+// Stage 1 table: x^e for e = 2 .. emax-1 of every (system, variable, point).
+template <class A>
+__global__ void powers_kernel(const PowerParams pp) {
+  constexpr int KD = A::kDoubles;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < pp.total; idx += stride) {
+    int n, emax, P;
+    int64_t local, pt_off, tab_off;
+    if (pp.single_P >= 0) {
+      n = pp.single_n;
+      emax = pp.single_emax;
+      P = pp.single_P;
+      local = idx;
+      pt_off = 0;
+      tab_off = 0;
+    } else {
+      int lo = 0, hi = pp.count;  // find s with prefix[s] <= idx < prefix[s+1]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pp.prefix[mid] <= idx) lo = mid; else hi = mid;
+      }
+      const SysDesc sd = pp.sys[lo];
+      n = sd.n;
+      emax = sd.emax;
+      P = sd.P;
+      local = idx - pp.prefix[lo];
+      pt_off = sd.pt_off;
+      tab_off = sd.tab_off;
+    }
+    const int64_t v = local / P, q = local - v * P;
+    const typename A::Full x = A::load_full(pp.points + (pt_off + v * P + q) * KD);
+    auto entry = [&](int e) { return pp.table + (tab_off + (static_cast<int64_t>(e - 2) * n + v) * P + q) * KD; };
+    // x^e = x^(e - h) * x^h with h = floor(e/2): one product per entry as in
+    // a running product, but a rounding chain of depth O(log e), not O(e).
+    for (int e = 2; e < emax; e++) {
+      const int h = e >> 1, g = e - h;
+      const typename A::Full lo = h == 1 ? x : A::load_coherent(entry(h));
+      const typename A::Full hi = g == 1 ? x : A::load_coherent(entry(g));
+      A::store_full(entry(e), A::cmul(hi, lo));
+    }
+  }
+}
+
+cudaError_t launch_powers(bool dd, const PowerParams &p, cudaStream_t s) {
+  if (p.total <= 0) return cudaSuccess;
+  const int threads = 256;
+  int64_t blocks = (p.total + threads - 1) / threads;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (dd)
+    powers_kernel<ArithDD><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
+  else
+    powers_kernel<ArithF64><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_main(bool dd, size_t smem_bytes) {
+  // Every handle launches with at most the device's opt-in limit; setting the
+  // attribute to that limit once keeps it valid for all handles.
+  const int v = static_cast<int>(smem_bytes);
+  return dd ? cudaFuncSetAttribute(main_kernel<ArithDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)
+            : cudaFuncSetAttribute(main_kernel<ArithF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+}
+
+cudaError_t main_occupancy(bool dd, int warps_per_block, size_t smem_bytes, int *blocks_per_sm) {
+  return dd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<ArithDD>, warps_per_block * 32,
+                                                            smem_bytes)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<ArithF64>, warps_per_block * 32,
+                                                            smem_bytes);
+}
+
+cudaError_t launch_main(bool dd, const MainParams &p, int warps_per_block, size_t smem_bytes, int grid,
+                        cudaStream_t s) {
+  if (p.n_items <= 0) return cudaSuccess;
+  if (dd)
+    main_kernel<ArithDD><<<grid, warps_per_block * 32, smem_bytes, s>>>(p);
+  else
+    main_kernel<ArithF64><<<grid, warps_per_block * 32, smem_bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 issue-rate probe: independent FMA chains on every SM.
+// ---------------------------------------------------------------------------
+
+__global__ void fp64_probe_kernel(double *out, long long *cycles, int iters) {
+  double acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) acc[i] = threadIdx.x * 1e-3 + i;
+  const double a = 1.0000001, b = 1e-9;
+  const long long c0 = clock64();
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) acc[i] = __fma_rn(acc[i], a, b);
+  }
+  const long long c1 = clock64();
+  double sum = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) sum += acc[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+  if (threadIdx.x == 0) cycles[blockIdx.x] = c1 - c0;
+}
+
+cudaError_t fp64_peak_probe(cudaStream_t s, double *fma_per_s, double *sm_clock_mhz) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int blocks = sms * 4, threads = 256, iters = 1000;
+  double *out = nullptr;
+  long long *cyc = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  long long *hc = nullptr;
+  if ((e = cudaMalloc(&out, sizeof(double) * blocks * threads)) != cudaSuccess) goto done;
+  if ((e = cudaMalloc(&cyc, sizeof(long long) * blocks)) != cudaSuccess) goto done;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) goto done;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) goto done;
+  fp64_probe_kernel<<<blocks, threads, 0, s>>>(out, cyc, 64);  // warm-up
+  cudaEventRecord(e0, s);
+  fp64_probe_kernel<<<blocks, threads, 0, s>>>(out, cyc, iters);
+  cudaEventRecord(e1, s);
+  if ((e = cudaEventSynchronize(e1)) != cudaSuccess) goto done;
+  if ((e = cudaGetLastError()) != cudaSuccess) goto done;
+  {
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    hc = new long long[blocks];
+    if ((e = cudaMemcpy(hc, cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost)) != cudaSuccess) goto done;
+    long long mc = 0;
+    for (int i = 0; i < blocks; i++) mc = hc[i] > mc ? hc[i] : mc;
+    const double ops = static_cast<double>(blocks) * threads * iters * 8.0;
+    if (fma_per_s) *fma_per_s = ops / (ms * 1e-3);
+    if (sm_clock_mhz) *sm_clock_mhz = static_cast<double>(mc) / (ms * 1e-3) / 1e6;
+  }
+done:
+  delete[] hc;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (out) cudaFree(out);
+  if (cyc) cudaFree(cyc);
+  return e;
+}
+
+}  // namespace pe

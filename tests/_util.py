@@ -1,0 +1,108 @@
+"""Helpers shared by the tests: running the CUDA path and measuring errors.
+
+Error measure (the one the accuracy targets are stated in): for an output z
+with exact value z*, |z - z*| / S where S is the same sum over absolute
+values (S_f = sum |c| |x^a|, S_J = sum |c| a_i |x^(a-e_i)|).  Outputs whose S
+is zero must be exactly zero.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+DD_TOL = 1e-28
+F64_TOL = 1e-13
+
+
+def widen(x2):
+    """[..., 2] complex doubles -> [..., 4] complex double-doubles with zero low words."""
+    out = np.zeros(x2.shape[:-1] + (4,))
+    out[..., 0] = x2[..., 0]
+    out[..., 2] = x2[..., 1]
+    return out
+
+
+def fp64_inputs(system, pts):
+    """The inputs of the complex-double path, as double-doubles with zero low words."""
+    p = pts.copy()
+    p[..., 1] = 0.0
+    p[..., 3] = 0.0
+    return system.as_fp64(), p
+
+
+def to_device(pts, dd=True):
+    import torch
+
+    a = pts if dd else np.ascontiguousarray(pts[..., [0, 2]])
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def run(system, pts, dd=True, max_points=None):
+    """Evaluate with the CUDA library; returns numpy f [N,P,4], J [N,n,P,4]."""
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+
+    P = pts.shape[1]
+    ev = pkg.PolyEval(system if dd else system.as_fp64(), pkg.PE_DD if dd else pkg.PE_F64,
+                      max_points=max(P, 1) if max_points is None else max_points)
+    f, J = ev.eval(to_device(pts, dd))
+    torch.cuda.synchronize()
+    assert ev.status() == pkg.PE_OK
+    f, J = f.cpu().numpy(), J.cpu().numpy()
+    ev.close()
+    if not dd:
+        f, J = widen(f), widen(J)
+    return f, J
+
+
+def scales(system, pts):
+    """Normwise scales for all points: S_f [N, P], S_J [N, n, P] (float64).
+
+    Vectorised over monomials; the product over all variables but one is
+    taken from exclusive prefix and suffix products, so zero coordinates are
+    handled exactly."""
+    n, N, P = system.n_vars, system.n_polys, pts.shape[1]
+    M = system.n_monos
+    Sf = np.zeros((N, P))
+    SJ = np.zeros((N, n, P))
+    if M == 0:
+        return Sf, SJ
+    k = np.diff(system.mono_ptr).astype(np.int64)
+    kmax = int(k.max()) if k.size else 0
+    poly_of = np.repeat(np.arange(N), np.diff(system.poly_ptr))
+    ac = np.hypot(system.coef[:, 0], system.coef[:, 2])
+    rows = np.repeat(np.arange(M), k)
+    cols = np.arange(system.pos.size) - np.repeat(system.mono_ptr[:-1], k)
+    ax_all = np.hypot(pts[..., 0], pts[..., 2])  # [n, P]
+    for q in range(P):
+        ax = ax_all[:, q]
+        W = np.ones((M, max(kmax, 1)))
+        Wd = np.ones((M, max(kmax, 1)))
+        W[rows, cols] = ax[system.pos] ** system.exp
+        Wd[rows, cols] = system.exp * ax[system.pos] ** (system.exp - 1)
+        pre = np.cumprod(np.concatenate([np.ones((M, 1)), W[:, :-1]], axis=1), axis=1)
+        suf = np.cumprod(np.concatenate([np.ones((M, 1)), W[:, :0:-1]], axis=1), axis=1)[:, ::-1]
+        full = pre[:, -1] * W[:, -1]
+        np.add.at(Sf[:, q], poly_of, ac * full)
+        d = ac[rows] * Wd[rows, cols] * pre[rows, cols] * suf[rows, cols]
+        np.add.at(SJ[:, :, q], (poly_of[rows], system.pos), d)
+    return Sf, SJ
+
+
+def dd_diff(a, b):
+    """|a - b| for complex double-double arrays [..., 4], in float64."""
+    re = (a[..., 0] - b[..., 0]) + (a[..., 1] - b[..., 1])
+    im = (a[..., 2] - b[..., 2]) + (a[..., 3] - b[..., 3])
+    return np.hypot(re, im)
+
+
+def normwise_vs(a, b, S):
+    """Largest |a - b| / S; entries with S == 0 must agree exactly (inf if not)."""
+    d = dd_diff(a, b)
+    zero = S == 0
+    if np.any(zero):
+        if not (np.all(a[zero] == 0.0) and np.all(b[zero] == 0.0)):
+            return np.inf
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(zero, 0.0, d / np.where(zero, 1.0, S))
+    return float(np.max(r)) if r.size else 0.0

@@ -1,0 +1,107 @@
+"""The C ABI without a GPU: the library loads, exports every entry point the
+header declares, and host-side validation rejects malformed systems
+(Section 2, Eq. 1: sparse monomials with sorted positions, exponents >= 1,
+nonzero coefficients)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1201_0499_gb300 as pkg
+    from paper_1201_0499_gb300 import build
+
+    build.build()
+    pkg.load_library()
+    return pkg
+
+
+def declared_entry_points():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"^PE_API\s+[\w\s\*]*?\b(polyeval_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_entry_points()
+    for required in ["polyeval_create", "polyeval_eval", "polyeval_destroy", "polyeval_create_many",
+                     "polyeval_eval_many", "polyeval_status", "polyeval_strerror", "polyeval_validate"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(pkg):
+    lib = pkg.load_library()
+    for name in declared_entry_points():
+        assert hasattr(lib, name), name
+    # and the binding has a function of the same name for each
+    for name in declared_entry_points():
+        assert hasattr(pkg, name), name
+
+
+def test_strerror(pkg):
+    assert pkg.polyeval_strerror(pkg.PE_OK) == "ok"
+    for c in (pkg.PE_EINVAL, pkg.PE_ENOMEM, pkg.PE_ECUDA, pkg.PE_ERANGE, pkg.PE_EDEVICE):
+        assert pkg.polyeval_strerror(c) != "unknown status code"
+    assert pkg.polyeval_strerror(12345) == "unknown status code"
+
+
+def _small():
+    return synth.from_monomials(4, [[([0, 2], [3, 1]), ([1], [2])], [([], []), ([0, 1, 2, 3], [1, 1, 1, 1])]],
+                                [[1, 0, 0.5, 0], [2, 0, 0, 0], [0, 0, 1, 0], [1, 1e-17, -1, 0]])
+
+
+def _mutate(s, **kw):
+    import copy
+
+    t = copy.deepcopy(s)
+    for k, v in kw.items():
+        setattr(t, k, v)
+    return t
+
+
+def test_validate_accepts_good_systems(pkg):
+    assert pkg.polyeval_validate(_small()) == pkg.PE_OK
+    s, _ = synth.config(1)
+    assert pkg.polyeval_validate(s) == pkg.PE_OK
+    empty = synth.from_monomials(3, [], np.zeros((0, 4)))
+    assert pkg.polyeval_validate(empty) == pkg.PE_OK
+
+
+def test_validate_rejects(pkg):
+    s = _small()
+    E, R = pkg.PE_EINVAL, pkg.PE_ERANGE
+    assert pkg.polyeval_validate(_mutate(s, n_vars=0)) == E
+    assert pkg.polyeval_validate(_mutate(s, n_vars=70000)) == R
+    pos = s.pos.copy(); pos[0] = 4
+    assert pkg.polyeval_validate(_mutate(s, pos=pos)) == E          # position >= n
+    pos = s.pos.copy(); pos[0], pos[1] = pos[1], pos[0]
+    assert pkg.polyeval_validate(_mutate(s, pos=pos)) == E          # not increasing
+    pos = s.pos.copy(); pos[1] = pos[0]
+    assert pkg.polyeval_validate(_mutate(s, pos=pos)) == E          # duplicate position
+    pos = s.pos.copy(); pos[0] = -1
+    assert pkg.polyeval_validate(_mutate(s, pos=pos)) == E
+    ex = s.exp.copy(); ex[0] = 0
+    assert pkg.polyeval_validate(_mutate(s, exp=ex)) == E           # exponent 0
+    ex = s.exp.copy(); ex[0] = 257
+    assert pkg.polyeval_validate(_mutate(s, exp=ex)) == R           # above PE_MAX_EXP
+    ex = s.exp.copy(); ex[0] = 256
+    assert pkg.polyeval_validate(_mutate(s, exp=ex)) == pkg.PE_OK
+    c = s.coef.copy(); c[1] = 0
+    assert pkg.polyeval_validate(_mutate(s, coef=c)) == E           # c = 0 (Eq. 1 asks c != 0)
+    assert pkg.polyeval_validate(_mutate(s, coef=c), pkg.PE_ALLOW_ZERO_COEF) == pkg.PE_OK
+    c = s.coef.copy(); c[0, 1] = np.nan
+    assert pkg.polyeval_validate(_mutate(s, coef=c)) == E
+    pp = s.poly_ptr.copy(); pp[0] = 1
+    assert pkg.polyeval_validate(_mutate(s, poly_ptr=pp)) == E
+    mp = s.mono_ptr.copy(); mp[2] = mp[1] - 1
+    assert pkg.polyeval_validate(_mutate(s, mono_ptr=mp)) == E
