@@ -221,6 +221,41 @@ PE_API int polyeval_timing_read(polyeval_t *h, double *total_ms, int64_t *launch
  */
 PE_API int polyeval_status(polyeval_t *h);
 
+/*
+ * Evaluation for callers that cannot allocate device memory.  (This entry
+ * point has no counterpart in the paper; it is a deployment variant of
+ * polyeval_eval.)
+ *
+ * A caller whose device memory belongs to another allocator (a framework's
+ * caching allocator, a pre-reserved arena, a fixed start-up budget) cannot
+ * let this library call cudaMalloc, and so cannot use polyeval_create.  This
+ * entry point allocates nothing: the caller passes the system, the points
+ * and the outputs in its own device memory, and the only scratch -- the
+ * table of powers of Section 3.1 -- lives in a static 16 MiB device array
+ * that every GPU loading the library holds until the process exits.
+ *
+ *   dev_sys   host struct in the pe_system format whose pointer fields
+ *             (poly_ptr, mono_ptr, pos, exp, coef) are DEVICE pointers; the
+ *             arrays must satisfy what polyeval_validate checks (they are not
+ *             read on the host)
+ *   max_k     an upper bound on the variables of any monomial (<= 256)
+ *   max_exp   an upper bound on any exponent (<= PE_MAX_EXP)
+ *   points, P, out_f, out_J, stream   as polyeval_eval, complex
+ *             double-double (pe_cdd) only
+ * Limits: (max_exp - 2) * n_vars * P complex double-doubles must fit in the
+ * 16 MiB array (524288 of them), else PE_ERANGE; PE_EINVAL for null pointers
+ * or negative sizes.  A monomial breaking max_k, max_exp or 0 <= pos < n is
+ * skipped and f of its polynomial is written as NaN.
+ * The first call on a device looks up the array's device address (and sets
+ * the kernel's shared-memory limit) with that device current; make that
+ * first call before any stream capture.  Every call uses the same array:
+ * each call writes all the table entries it reads before reading them, so
+ * nothing has to start at zero, but calls that overlap on the GPU (other
+ * streams or host threads) race on it.
+ */
+PE_API int polyeval_eval_noalloc(const pe_system *dev_sys, int32_t max_k, int32_t max_exp, const void *points,
+                                 int64_t P, void *out_f, void *out_J, void *stream);
+
 /* Free a handle and its device memory (NULL is accepted). */
 PE_API void polyeval_destroy(polyeval_t *h);
 

@@ -31,6 +31,7 @@ from ._binding import (  # noqa: F401
     polyeval_eval,
     polyeval_eval_host,
     polyeval_eval_many,
+    polyeval_eval_noalloc,
     polyeval_fp64_peak,
     polyeval_many_layout,
     polyeval_status,

@@ -84,6 +84,7 @@ def load_library(path: Optional[str] = None):
         "polyeval_destroy": ([P], None),
         "polyeval_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "polyeval_fp64_peak": ([P, D, D], ctypes.c_int),
+        "polyeval_eval_noalloc": ([ctypes.POINTER(pe_system), I32, I32, P, I64, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -224,6 +225,17 @@ def polyeval_fp64_peak(stream=None):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(load_library().polyeval_fp64_peak(_stream(stream), ctypes.byref(a), ctypes.byref(b)), "polyeval_fp64_peak")
     return a.value, b.value
+
+
+def polyeval_eval_noalloc(dev_sys: pe_system, max_k: int, max_exp: int, points, P: int, out_f, out_J,
+                          stream=None) -> None:
+    """For callers that cannot let the library allocate device memory:
+    ``dev_sys`` is a pe_system whose array fields hold device addresses (for
+    example of torch tensors the caller owns); scratch comes from a static
+    device array inside the library."""
+    _check(load_library().polyeval_eval_noalloc(ctypes.byref(dev_sys), int(max_k), int(max_exp), _addr(points),
+                                                int(P), _addr(out_f), _addr(out_J), _stream(stream)),
+           "polyeval_eval_noalloc")
 
 
 # ----------------------------------------------------------------------------
