@@ -66,6 +66,13 @@ extern "C" {
 /* ---- precisions -------------------------------------------------------- */
 #define PE_DD 0  /* complex double-double (pe_cdd in and out)  */
 #define PE_F64 1 /* complex double        (pe_c64 in and out)  */
+/* Complex double-double in and out (pe_cdd), products computed in complex
+ * block floating point with 128-bit integer mantissas on the integer pipes
+ * (error about 2^-120 per product relative to the operands' magnitudes),
+ * sums in double-double.  Same method and layouts as PE_DD; more accurate
+ * and, on GB300 where FP64 issues about 36x slower than integer multiply-add,
+ * faster. */
+#define PE_DD_INT 2
 
 /* ---- flags for polyeval_create / polyeval_create_many / polyeval_validate */
 #define PE_ALLOW_ZERO_COEF 1u /* accept c = 0 (Eq. 1 asks c != 0); for tests */
@@ -125,7 +132,7 @@ PE_API int polyeval_validate(const pe_system *sys, uint32_t flags);
 /*
  * Compile one system for evaluation (Section 2 format -> device metadata).
  *   sys         host system, copied; the caller may free it on return
- *   precision   PE_DD or PE_F64
+ *   precision   PE_DD, PE_F64 or PE_DD_INT
  *   flags       PE_ALLOW_ZERO_COEF or 0
  *   max_points  largest P any later polyeval_eval call will pass (>= 1);
  *               sizes the table of powers (Section 3.1) kept on the device
@@ -140,7 +147,7 @@ PE_API int polyeval_create(const pe_system *sys, int precision, uint32_t flags, 
 
 /*
  * Evaluate f and J at P points (Sections 3.1-3.3).
- *   points  device, [n_vars][P] pe_cdd (PE_DD) or pe_c64 (PE_F64)
+ *   points  device, [n_vars][P] pe_cdd (PE_DD, PE_DD_INT) or pe_c64 (PE_F64)
  *   P       number of points, 0 <= P <= max_points (0 returns PE_OK at once)
  *   out_f   device, [n_polys][P] of the same element type
  *   out_J   device, [n_polys][n_vars][P] of the same element type
@@ -198,7 +205,8 @@ PE_API int polyeval_eval_many(polyeval_t *h, const void *points, void *out_f, vo
  * handle's systems (for a batch: over all points of all systems, i.e. one
  * whole polyeval_eval_many):
  *   fp64_ops    double-precision instructions (add, mul, fma) the method
- *               executes, counted from the compiled system
+ *               executes, counted from the compiled system (for PE_DD_INT:
+ *               those of its double-double sums)
  *   fp64_flops  the same with an fma counted as 2 flops
  * Either pointer may be NULL.
  */

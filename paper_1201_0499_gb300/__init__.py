@@ -10,6 +10,7 @@ from ._binding import (  # noqa: F401
     LIB_PATH,
     PE_ALLOW_ZERO_COEF,
     PE_DD,
+    PE_DD_INT,
     PE_ECUDA,
     PE_EDEVICE,
     PE_EINVAL,

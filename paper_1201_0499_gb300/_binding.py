@@ -27,6 +27,7 @@ PE_EDEVICE = -5
 
 PE_DD = 0
 PE_F64 = 1
+PE_DD_INT = 2
 
 PE_ALLOW_ZERO_COEF = 1
 
@@ -243,7 +244,7 @@ def polyeval_eval_noalloc(dev_sys: pe_system, max_k: int, max_exp: int, points, 
 # ----------------------------------------------------------------------------
 
 def _elem(precision: int) -> int:
-    return 4 if precision == PE_DD else 2
+    return 2 if precision == PE_F64 else 4
 
 
 class PolyEval:

@@ -52,7 +52,8 @@ struct DeviceBuf {
 }  // namespace
 
 struct polyeval {
-  bool dd = true;
+  bool dd = true;     // complex double-double points and outputs (PE_DD, PE_DD_INT)
+  bool wide = false;  // products on the integer pipes (PE_DD_INT)
   bool batch = false;
   int32_t count = 0;
   int64_t max_points = 0;
@@ -68,7 +69,7 @@ struct polyeval {
   int64_t power_total_batch = 0;
   double ops_per_point = 0.0, flops_per_point = 0.0;  // single: per point; batch: per whole evaluation
   // device memory
-  DeviceBuf poly_ptr, mono_ptr, var, coef, poly_sys, sysd, perm, items, prefix, table, counter, status;
+  DeviceBuf poly_ptr, mono_ptr, var, coef, coef_wide, poly_sys, sysd, perm, items, prefix, table, counter, status;
   DeviceBuf stage_pts, stage_f, stage_J;
   // timing of the main kernel
   bool timing = false;
@@ -83,6 +84,20 @@ struct polyeval {
 namespace {
 
 int elem_doubles(const polyeval *h) { return h->dd ? 4 : 2; }
+
+// Table of powers: entries per (variable, point) and bytes per entry.  The
+// double-double and double tables hold x^2 .. x^(emax-1); the block-format
+// table also holds x itself (entry 1).
+int64_t table_levels(const polyeval *h, int emax) {
+  return h->wide ? std::max(emax - 1, 1) : std::max(emax - 2, 0);
+}
+size_t table_entry_bytes(const polyeval *h) { return h->wide ? pe::kWideBytes : elem_doubles(h) * sizeof(double); }
+
+// Launch the power-table kernel of the handle's precision.
+int run_powers(const polyeval *h, const pe::PowerParams &pp, cudaStream_t s) {
+  const cudaError_t e = h->wide ? pe::launch_powers_wide(pp, s) : pe::launch_powers(h->dd, pp, s);
+  return e == cudaSuccess ? PE_OK : PE_ECUDA;
+}
 
 // FP64 instructions and flops per point for one monomial (k variables, n2 of
 // them with exponent >= 2), as the main kernel executes them (both lanes of
@@ -110,6 +125,10 @@ Cost monomial_cost(bool dd, int k, int n2) {
   }
   return c;
 }
+
+// PE_DD_INT: only the double-double sums run on the FP64 pipe (5 DADD per
+// lane per term); the products are integer instructions.
+Cost monomial_cost_wide(int k) { return Cost{10.0 * (k + 1), 10.0 * (k + 1)}; }
 
 // Per point and per polynomial: renormalising the row (double-double only)
 // and finishing f.
@@ -161,7 +180,7 @@ struct Compiled {
   int32_t kmax = 0;
 };
 
-int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, SysDesc &d) {
+int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, bool wide, SysDesc &d) {
   d.n = s->n_vars;
   d.N = s->n_polys;
   d.poly0 = static_cast<int32_t>(c.poly_sys.size());
@@ -180,13 +199,13 @@ int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, S
       }
       const int k = static_cast<int>(e - b);
       c.kmax = std::max(c.kmax, k);
-      const Cost mc = monomial_cost(dd, k, n2);
+      const Cost mc = wide ? monomial_cost_wide(k) : monomial_cost(dd, k, n2);
       pc.ops += mc.ops;
       pc.flops += mc.flops;
       if (c.var.size() > static_cast<size_t>(INT32_MAX - 1)) return PE_ERANGE;
       c.mono_ptr.push_back(static_cast<int32_t>(c.var.size()));
       const pe_cdd &cf = s->coef[t];
-      if (dd) {
+      if (dd || wide) {
         c.coef.insert(c.coef.end(), {cf.re_hi, cf.re_lo, cf.im_hi, cf.im_lo});
       } else {
         c.coef.insert(c.coef.end(), {cf.re_hi, cf.im_hi});
@@ -210,15 +229,23 @@ int finish_handle(polyeval *h, Compiled &c) {
   if (cudaGetDevice(&dev) != cudaSuccess) return PE_ECUDA;
   if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PE_ECUDA;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return PE_ECUDA;
-  const size_t per_warp = static_cast<size_t>(h->kslots) * 32 * (h->dd ? 16 : 8);
+  const size_t per_warp =
+      static_cast<size_t>(h->kslots) * 32 * (h->wide ? pe::kWideSlotBytes : (h->dd ? 16 : 8));
   h->warps_per_block = pe::kWarpsPerBlockMax;
   while (h->warps_per_block > 1 && per_warp * h->warps_per_block > static_cast<size_t>(optin)) h->warps_per_block /= 2;
   if (per_warp * h->warps_per_block > static_cast<size_t>(optin)) return PE_ERANGE;
   h->smem_bytes = per_warp * h->warps_per_block;
   h->smem_per_warp = per_warp;
-  if (pe::prepare_main(h->dd, static_cast<size_t>(optin)) != cudaSuccess) return PE_ECUDA;
-  if (pe::main_occupancy(h->dd, h->warps_per_block, h->smem_bytes, &h->blocks_per_sm) != cudaSuccess) return PE_ECUDA;
-  if (pe::main_occupancy(h->dd, 1, per_warp, &h->blocks_per_sm_1) != cudaSuccess) return PE_ECUDA;
+  if (h->wide) {
+    if (pe::prepare_main_wide(static_cast<size_t>(optin)) != cudaSuccess) return PE_ECUDA;
+    if (pe::main_wide_occupancy(h->warps_per_block, h->smem_bytes, &h->blocks_per_sm) != cudaSuccess) return PE_ECUDA;
+    if (pe::main_wide_occupancy(1, per_warp, &h->blocks_per_sm_1) != cudaSuccess) return PE_ECUDA;
+  } else {
+    if (pe::prepare_main(h->dd, static_cast<size_t>(optin)) != cudaSuccess) return PE_ECUDA;
+    if (pe::main_occupancy(h->dd, h->warps_per_block, h->smem_bytes, &h->blocks_per_sm) != cudaSuccess)
+      return PE_ECUDA;
+    if (pe::main_occupancy(h->dd, 1, per_warp, &h->blocks_per_sm_1) != cudaSuccess) return PE_ECUDA;
+  }
   if (h->blocks_per_sm < 1 || h->blocks_per_sm_1 < 1) return PE_ERANGE;
   int rc;
   if ((rc = h->poly_ptr.upload(c.poly_ptr)) || (rc = h->mono_ptr.upload(c.mono_ptr)) || (rc = h->var.upload(c.var)) ||
@@ -226,6 +253,15 @@ int finish_handle(polyeval *h, Compiled &c) {
     return rc;
   if ((rc = h->counter.alloc(sizeof(unsigned))) || (rc = h->status.alloc(sizeof(int)))) return rc;
   if (cudaMemset(h->status.p, 0, sizeof(int)) != cudaSuccess) return PE_ECUDA;
+  if (h->wide) {  // coefficients to the block format, once
+    const int64_t M = static_cast<int64_t>(c.coef.size() / 4);
+    if ((rc = h->coef_wide.alloc(static_cast<size_t>(M) * pe::kWideBytes)) != PE_OK) return rc;
+    if (pe::convert_coef_wide(static_cast<const double *>(h->coef.p), static_cast<uint32_t *>(h->coef_wide.p), M,
+                              nullptr) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+      return PE_ECUDA;
+    h->coef.alloc(0);
+  }
   return PE_OK;
 }
 
@@ -251,7 +287,7 @@ pe::MainParams main_params(const polyeval *h) {
   p.poly_ptr = static_cast<const int32_t *>(h->poly_ptr.p);
   p.mono_ptr = static_cast<const int32_t *>(h->mono_ptr.p);
   p.var = static_cast<const uint32_t *>(h->var.p);
-  p.coef = static_cast<const double *>(h->coef.p);
+  p.coef = static_cast<const double *>(h->wide ? h->coef_wide.p : h->coef.p);
   p.poly_sys = static_cast<const int32_t *>(h->poly_sys.p);
   p.sys = static_cast<const SysDesc *>(h->sysd.p);
   p.perm = static_cast<const int32_t *>(h->perm.p);
@@ -279,7 +315,9 @@ int run_main(polyeval *h, const pe::MainParams &mp, cudaStream_t s) {
   }
   if (e0 && cudaEventRecord(e0, s) != cudaSuccess) return PE_ECUDA;
   const Shape sh = shape_for(h, mp.n_items);
-  if (pe::launch_main(h->dd, mp, sh.warps, sh.smem, sh.grid, s) != cudaSuccess) return PE_ECUDA;
+  const cudaError_t le = h->wide ? pe::launch_main_wide(mp, sh.warps, sh.smem, sh.grid, s)
+                                 : pe::launch_main(h->dd, mp, sh.warps, sh.smem, sh.grid, s);
+  if (le != cudaSuccess) return PE_ECUDA;
   if (e1 && cudaEventRecord(e1, s) != cudaSuccess) return PE_ECUDA;
   return PE_OK;
 }
@@ -293,20 +331,21 @@ int polyeval_validate(const pe_system *sys, uint32_t flags) { return validate(sy
 int polyeval_create(const pe_system *sys, int precision, uint32_t flags, int64_t max_points, polyeval_t **out) {
   if (!out) return PE_EINVAL;
   *out = nullptr;
-  if (precision != PE_DD && precision != PE_F64) return PE_EINVAL;
+  if (precision != PE_DD && precision != PE_F64 && precision != PE_DD_INT) return PE_EINVAL;
   if (max_points < 1) return PE_EINVAL;
   int rc = validate(sys, flags);
   if (rc != PE_OK) return rc;
   polyeval *h = nullptr;
   try {
     h = new polyeval();
-    h->dd = precision == PE_DD;
+    h->dd = precision != PE_F64;
+    h->wide = precision == PE_DD_INT;
     h->batch = false;
     h->count = 1;
     h->max_points = max_points;
     h->sys.resize(1);
     Compiled c;
-    if ((rc = append_system(c, sys, 0, h->dd, h->sys[0])) != PE_OK) {
+    if ((rc = append_system(c, sys, 0, h->dd, h->wide, h->sys[0])) != PE_OK) {
       delete h;
       return rc;
     }
@@ -328,16 +367,17 @@ int polyeval_create(const pe_system *sys, int precision, uint32_t flags, int64_t
       ops += c.poly_ops[p];
       flops += c.poly_flops[p];
     }
-    const Cost pw = power_cost(h->dd, d.emax);
+    const Cost pw = h->wide ? Cost{} : power_cost(h->dd, d.emax);
     h->ops_per_point = ops + pw.ops * d.n;
     h->flops_per_point = flops + pw.flops * d.n;
     if ((rc = finish_handle(h, c)) != PE_OK || (rc = h->perm.upload(perm)) != PE_OK) {
       delete h;
       return rc;
     }
-    if (d.emax > 2) {
-      const size_t entries = static_cast<size_t>(d.emax - 2) * d.n * static_cast<size_t>(max_points);
-      if ((rc = h->table.alloc(entries * elem_doubles(h) * sizeof(double))) != PE_OK) {
+    const int64_t levels = table_levels(h, d.emax);
+    if (levels > 0) {
+      const size_t entries = static_cast<size_t>(levels) * d.n * static_cast<size_t>(max_points);
+      if ((rc = h->table.alloc(entries * table_entry_bytes(h))) != PE_OK) {
         delete h;
         return rc;
       }
@@ -355,7 +395,7 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
   if (!out) return PE_EINVAL;
   *out = nullptr;
   if (!systems || !points_per_system || count < 1) return PE_EINVAL;
-  if (precision != PE_DD && precision != PE_F64) return PE_EINVAL;
+  if (precision != PE_DD && precision != PE_F64 && precision != PE_DD_INT) return PE_EINVAL;
   for (int32_t s = 0; s < count; s++) {
     int rc = validate(&systems[s], flags);
     if (rc != PE_OK) return rc;
@@ -365,7 +405,8 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
   int rc = PE_OK;
   try {
     h = new polyeval();
-    h->dd = precision == PE_DD;
+    h->dd = precision != PE_F64;
+    h->wide = precision == PE_DD_INT;
     h->batch = true;
     h->count = count;
     h->sys.resize(count);
@@ -380,7 +421,7 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
     double ops = 0, flops = 0;
     for (int32_t s = 0; s < count; s++) {
       SysDesc &d = h->sys[s];
-      if ((rc = append_system(c, &systems[s], s, h->dd, d)) != PE_OK) {
+      if ((rc = append_system(c, &systems[s], s, h->dd, h->wide, d)) != PE_OK) {
         delete h;
         return rc;
       }
@@ -394,10 +435,10 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
       pt += static_cast<int64_t>(d.n) * P;
       fo += static_cast<int64_t>(d.N) * P;
       jo += static_cast<int64_t>(d.N) * d.n * P;
-      const bool tab = d.emax > 2 && P > 0;
-      to += tab ? static_cast<int64_t>(d.emax - 2) * d.n * P : 0;
+      const bool tab = table_levels(h, d.emax) > 0 && P > 0;
+      to += tab ? table_levels(h, d.emax) * d.n * P : 0;
       prefix.push_back(prefix.back() + (tab ? static_cast<int64_t>(d.n) * P : 0));
-      const Cost pw = power_cost(h->dd, d.emax);
+      const Cost pw = h->wide ? Cost{} : power_cost(h->dd, d.emax);
       ops += pw.ops * d.n * P;
       flops += pw.flops * d.n * P;
       for (int32_t p = 0; p < d.N; p++) {
@@ -426,8 +467,8 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
     h->ops_per_point = ops;
     h->flops_per_point = flops;
     if ((rc = finish_handle(h, c)) != PE_OK || (rc = h->items.upload(it2)) != PE_OK ||
-        (rc = h->prefix.upload(prefix)) != PE_OK || (rc = h->table.alloc(static_cast<size_t>(to) * elem_doubles(h) *
-                                                                          sizeof(double))) != PE_OK) {
+        (rc = h->prefix.upload(prefix)) != PE_OK ||
+        (rc = h->table.alloc(static_cast<size_t>(to) * table_entry_bytes(h))) != PE_OK) {
       delete h;
       return rc;
     }
@@ -465,7 +506,7 @@ int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, voi
   if (!points || (!out_f && h->sys[0].N > 0) || (!out_J && h->sys[0].N > 0)) return PE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const SysDesc &d = h->sys[0];
-  if (d.emax > 2) {
+  if (table_levels(h, d.emax) > 0) {
     pe::PowerParams pp{};
     pp.sys = static_cast<const SysDesc *>(h->sysd.p);
     pp.points = static_cast<const double *>(points);
@@ -475,7 +516,7 @@ int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, voi
     pp.single_P = static_cast<int32_t>(P);
     pp.single_n = d.n;
     pp.single_emax = d.emax;
-    if (pe::launch_powers(h->dd, pp, s) != cudaSuccess) return PE_ECUDA;
+    if (run_powers(h, pp, s) != PE_OK) return PE_ECUDA;
   }
   pe::MainParams mp = main_params(h);
   mp.points = static_cast<const double *>(points);
@@ -501,7 +542,7 @@ int polyeval_eval_many(polyeval_t *h, const void *points, void *out_f, void *out
     pp.total = h->power_total_batch;
     pp.count = h->count;
     pp.single_P = -1;
-    if (pe::launch_powers(h->dd, pp, s) != cudaSuccess) return PE_ECUDA;
+    if (run_powers(h, pp, s) != PE_OK) return PE_ECUDA;
   }
   pe::MainParams mp = main_params(h);
   mp.points = static_cast<const double *>(points);

@@ -70,4 +70,14 @@ cudaError_t main_occupancy(bool dd, int warps_per_block, size_t smem_bytes, int 
 cudaError_t prepare_main(bool dd, size_t smem_bytes);
 cudaError_t fp64_peak_probe(cudaStream_t s, double *fma_per_s, double *sm_clock_mhz);
 
+// Integer-pipe evaluation (kernels_wide.cu): 128-bit block floating point
+// products, double-double sums.  Table entries and coefficients are 48 bytes.
+constexpr int kWideBytes = 48;
+constexpr int kWideSlotBytes = 6 * 4;  // per lane and prefix-product slot
+cudaError_t convert_coef_wide(const double *coef_dd, uint32_t *coef_wide, int64_t M, cudaStream_t s);
+cudaError_t launch_powers_wide(const PowerParams &p, cudaStream_t s);
+cudaError_t prepare_main_wide(size_t smem_bytes);
+cudaError_t main_wide_occupancy(int warps_per_block, size_t smem_bytes, int *blocks_per_sm);
+cudaError_t launch_main_wide(const MainParams &p, int warps_per_block, size_t smem_bytes, int grid, cudaStream_t s);
+
 }  // namespace pe

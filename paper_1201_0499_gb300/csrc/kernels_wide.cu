@@ -1,0 +1,234 @@
+// Kernels of the integer-pipe evaluation (precision PE_DD_INT): the same
+// method and work decomposition as kernels.cu (Sections 3.1-3.3 of the
+// paper), with every product in the 128-bit block floating point of
+// wide.cuh and the sums into f and J in double-double on the FP64 pipe, so
+// that the integer pipes carry the products and the FP64 pipe the sums.
+//
+//  * powers_wide: every point's variables converted to the block format and
+//    their powers x^2 .. x^(d-1), in a table [e-1][n][P] of 48-byte entries
+//    (entry e = 1 is x itself).
+//  * main_wide: one warp per (polynomial, tile of 16 points); lanes 2q and
+//    2q+1 hold the real and the imaginary part of point q.  Common factor
+//    with the coefficient folded in, forward products in shared memory
+//    ([slot][word][lane], conflict-free), value, backward running product,
+//    derivatives; each term is converted to a double-double and added into f
+//    (registers) or the row J[p, :] (read-modify-write in the output).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dd.cuh"
+#include "internal.h"
+#include "wide.cuh"
+
+namespace pe {
+
+using wide::WF;
+using wide::WV;
+
+constexpr int kWideWords = 12;  // 32-bit words per stored full value (48 bytes)
+constexpr int kSlotWords = 6;   // words per lane in a prefix-product slot
+
+__global__ void convert_coef_kernel(const double *coef_dd, uint32_t *coef_wide, int64_t M) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < M; t += stride) {
+    const double *c = coef_dd + t * 4;
+    wide::store_wf(coef_wide + t * kWideWords, wide::wf_from_cdd(c[0], c[1], c[2], c[3]));
+  }
+}
+
+__global__ void powers_wide(const PowerParams pp) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  uint32_t *table = reinterpret_cast<uint32_t *>(pp.table);
+  for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < pp.total; idx += stride) {
+    int n, emax, P;
+    int64_t local, pt_off, tab_off;
+    if (pp.single_P >= 0) {
+      n = pp.single_n;
+      emax = pp.single_emax;
+      P = pp.single_P;
+      local = idx;
+      pt_off = 0;
+      tab_off = 0;
+    } else {
+      int lo = 0, hi = pp.count;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pp.prefix[mid] <= idx) lo = mid; else hi = mid;
+      }
+      const SysDesc sd = pp.sys[lo];
+      n = sd.n;
+      emax = sd.emax;
+      P = sd.P;
+      local = idx - pp.prefix[lo];
+      pt_off = sd.pt_off;
+      tab_off = sd.tab_off;
+    }
+    const int64_t v = local / P, q = local - v * P;
+    const double *xp = pp.points + (pt_off + v * P + q) * 4;
+    auto entry = [&](int e) { return table + (tab_off + (static_cast<int64_t>(e - 1) * n + v) * P + q) * kWideWords; };
+    const WF x = wide::wf_from_cdd(xp[0], xp[1], xp[2], xp[3]);
+    wide::store_wf(entry(1), x);
+    for (int e = 2; e < emax; e++) {
+      const int h = e >> 1, g = e - h;
+      const WF a = h == 1 ? x : wide::load_wf_coherent(entry(h));
+      const WF b = g == 1 ? x : wide::load_wf_coherent(entry(g));
+      wide::store_wf(entry(e), wide::wf_mul(b, a));
+    }
+  }
+}
+
+__device__ __forceinline__ void store_slot(uint32_t *slots, int j, int lane, const WV &v) {
+  uint32_t *b = slots + j * (kSlotWords * 32) + lane;
+  b[0] = v.m.w0;
+  b[32] = v.m.w1;
+  b[64] = v.m.w2;
+  b[96] = v.m.w3;
+  b[128] = v.s;
+  b[160] = static_cast<uint32_t>(v.e);
+}
+
+__device__ __forceinline__ WV load_slot(const uint32_t *slots, int j, int lane) {
+  const uint32_t *b = slots + j * (kSlotWords * 32) + lane;
+  return WV{wide::Mag{b[0], b[32], b[64], b[96]}, b[128], static_cast<int32_t>(b[160])};
+}
+
+__device__ __forceinline__ void accumulate_dd(double *p, int c, bool valid, dd x) {
+  const double2 a = reinterpret_cast<const double2 *>(p)[c];
+  const dd s = add(dd{a.x, a.y}, x);
+  if (valid) reinterpret_cast<double2 *>(p)[c] = make_double2(s.h, s.l);
+}
+
+__device__ void process_item_wide(const MainParams &kp, int gp, int tile, int s, int P, uint32_t *slots, int lane) {
+  const SysDesc sd = kp.sys[s];
+  const int n = sd.n;
+  const int q = tile * kPointsPerWarp + (lane >> 1);
+  const bool valid = q < P;
+  const int qc = valid ? q : P - 1;
+  const int c = lane & 1;
+  const size_t Pz = static_cast<size_t>(P);
+  const int pl = gp - sd.poly0;
+  const uint32_t *Tb = reinterpret_cast<const uint32_t *>(kp.table) + static_cast<size_t>(sd.tab_off) * kWideWords;
+  const uint32_t *coef = reinterpret_cast<const uint32_t *>(kp.coef);
+  double *Jrow = kp.out_J + (static_cast<size_t>(sd.J_off) + static_cast<size_t>(pl) * n * Pz) * 4;
+
+  auto tel = [&](int e, int v) { return Tb + ((static_cast<size_t>(e - 1) * n + v) * Pz + qc) * kWideWords; };
+  auto jel = [&](int v) { return Jrow + (static_cast<size_t>(v) * Pz + qc) * 4; };
+
+  if (valid)
+    for (int v = 0; v < n; v++) reinterpret_cast<double2 *>(jel(v))[c] = make_double2(0.0, 0.0);
+
+  dd f{0.0, 0.0};
+  const int t0 = kp.poly_ptr[gp], t1 = kp.poly_ptr[gp + 1];
+  for (int t = t0; t < t1; t++) {
+    const int vb = kp.mono_ptr[t];
+    const int k = kp.mono_ptr[t + 1] - vb;
+    WV G = wide::component(wide::load_wf(coef + static_cast<size_t>(t) * kWideWords), c);
+    if (k == 0) {
+      f = add(f, wide::to_dd(G));
+      continue;
+    }
+    const uint32_t *vw = kp.var + vb;
+    // Stage 1: G = c * prod_{a_j >= 2} x_{i_j}^(a_j - 1)
+    for (int j = 0; j < k; j++) {
+      const uint32_t w = __ldg(vw + j);
+      const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
+      if (a >= 2) G = wide::mul_x(G, wide::load_wf(tel(a - 1, v)), c);
+    }
+    // Stage 2, forward: slot j <- G x_{i_1} ... x_{i_j}
+    WV Pc = G;
+    for (int j = 0; j < k - 1; j++) {
+      store_slot(slots, j, lane, Pc);
+      const int v = static_cast<int>(__ldg(vw + j) & 0xffffu);
+      Pc = wide::mul_x(Pc, wide::load_wf(tel(1, v)), c);
+    }
+    const uint32_t wl = __ldg(vw + k - 1);
+    const int vl = static_cast<int>(wl & 0xffffu), al = static_cast<int>(wl >> 16);
+    const WF xl = wide::load_wf(tel(1, vl));
+    f = add(f, wide::to_dd(wide::mul_x(Pc, xl, c)));
+    accumulate_dd(jel(vl), c, valid, wide::to_dd(al == 1 ? Pc : wide::mul_small(Pc, static_cast<uint32_t>(al))));
+    // Stage 2, backward
+    WV Q = wide::component(xl, c);
+    for (int j = k - 2; j >= 0; j--) {
+      const uint32_t w = __ldg(vw + j);
+      const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
+      const WV D = wide::mul_pair(load_slot(slots, j, lane), Q, c);
+      accumulate_dd(jel(v), c, valid, wide::to_dd(a == 1 ? D : wide::mul_small(D, static_cast<uint32_t>(a))));
+      if (j > 0) Q = wide::mul_x(Q, wide::load_wf(tel(1, v)), c);
+    }
+  }
+  if (valid) {
+    const dd fo = normalize(f);
+    reinterpret_cast<double2 *>(kp.out_f + (static_cast<size_t>(sd.f_off) + static_cast<size_t>(pl) * Pz + q) * 4)[c] =
+        make_double2(fo.h, fo.l);
+    for (int v = 0; v < n; v++) {
+      double2 *p = reinterpret_cast<double2 *>(jel(v)) + c;
+      const double2 a = *p;
+      const dd r = normalize(dd{a.x, a.y});
+      *p = make_double2(r.h, r.l);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlockMax * 32) main_wide(const MainParams kp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *slots = reinterpret_cast<uint32_t *>(smem_raw) + static_cast<size_t>(warp) * kp.kslots * kSlotWords * 32;
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(kp.counter, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (static_cast<int64_t>(item) >= kp.n_items) break;
+    int gp, tile, s, P;
+    if (kp.single_P >= 0) {
+      const int r = static_cast<int>(item) / kp.single_T;
+      tile = static_cast<int>(item) - r * kp.single_T;
+      gp = kp.perm[r];
+      s = 0;
+      P = kp.single_P;
+    } else {
+      const int2 it = kp.items[item];
+      gp = it.x;
+      tile = it.y;
+      s = (gp >= 0 && gp < kp.n_polys_total) ? kp.poly_sys[gp] : 0;
+      P = kp.sys[s].P;
+    }
+    if (gp < 0 || gp >= kp.n_polys_total || tile * kPointsPerWarp >= P) {
+      if (lane == 0) atomicOr(kp.status, 1);
+      continue;
+    }
+    process_item_wide(kp, gp, tile, s, P, slots, lane);
+  }
+}
+
+cudaError_t convert_coef_wide(const double *coef_dd, uint32_t *coef_wide, int64_t M, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  int64_t blocks = (M + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  convert_coef_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(coef_dd, coef_wide, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_powers_wide(const PowerParams &p, cudaStream_t s) {
+  if (p.total <= 0) return cudaSuccess;
+  int64_t blocks = (p.total + 127) / 128;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  powers_wide<<<static_cast<unsigned>(blocks), 128, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_main_wide(size_t smem_bytes) {
+  return cudaFuncSetAttribute(main_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
+}
+
+cudaError_t main_wide_occupancy(int warps_per_block, size_t smem_bytes, int *blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_wide, warps_per_block * 32, smem_bytes);
+}
+
+cudaError_t launch_main_wide(const MainParams &p, int warps_per_block, size_t smem_bytes, int grid, cudaStream_t s) {
+  if (p.n_items <= 0) return cudaSuccess;
+  main_wide<<<grid, warps_per_block * 32, smem_bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace pe

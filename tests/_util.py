@@ -12,6 +12,20 @@ import numpy as np
 DD_TOL = 1e-28
 F64_TOL = 1e-13
 
+# the precisions of the library: double-double, double, double-double with
+# integer-pipe products
+PRECS = ["dd", "f64", "ddint"]
+
+
+def tol(prec):
+    return F64_TOL if prec == "f64" else DD_TOL
+
+
+def pe_precision(prec):
+    import paper_1201_0499_gb300 as pkg
+
+    return {"dd": pkg.PE_DD, "f64": pkg.PE_F64, "ddint": pkg.PE_DD_INT}[prec]
+
 
 def widen(x2):
     """[..., 2] complex doubles -> [..., 4] complex double-doubles with zero low words."""
@@ -36,14 +50,20 @@ def to_device(pts, dd=True):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
 
 
-def run(system, pts, dd=True, max_points=None):
-    """Evaluate with the CUDA library; returns numpy f [N,P,4], J [N,n,P,4]."""
+def run(system, pts, prec="dd", max_points=None):
+    """Evaluate with the CUDA library; returns numpy f [N,P,4], J [N,n,P,4].
+    prec: "dd", "f64" or "ddint" (True/False stand for "dd"/"f64")."""
     import torch
 
     import paper_1201_0499_gb300 as pkg
 
+    if prec is True:
+        prec = "dd"
+    elif prec is False:
+        prec = "f64"
+    dd = prec != "f64"
     P = pts.shape[1]
-    ev = pkg.PolyEval(system if dd else system.as_fp64(), pkg.PE_DD if dd else pkg.PE_F64,
+    ev = pkg.PolyEval(system if dd else system.as_fp64(), pe_precision(prec),
                       max_points=max(P, 1) if max_points is None else max_points)
     f, J = ev.eval(to_device(pts, dd))
     torch.cuda.synchronize()

@@ -12,7 +12,7 @@ import pytest
 import synth
 from oracle import exact as E
 
-from _util import DD_TOL, F64_TOL, fp64_inputs, normwise_vs, run, scales, to_device
+from _util import DD_TOL, F64_TOL, PRECS, fp64_inputs, normwise_vs, run, scales, to_device, tol
 
 pytestmark = pytest.mark.gpu
 
@@ -57,16 +57,16 @@ def random_system(seed, n, N, m, kmin, kmax, emax, coef_mod=None):
 # small cases: every output against the exact oracle
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("dd", [True, False], ids=["dd", "f64"])
-def test_several_tiles_ragged_tail(dd):
+@pytest.mark.parametrize("prec", PRECS)
+def test_several_tiles_ragged_tail(prec):
     s = random_system(101, n=20, N=12, m=10, kmin=1, kmax=7, emax=5, coef_mod=(-6, 6))
     pts = synth.points(102, 20, 70, modulus_octaves=(-1, 0))  # 5 tiles of 16, last one ragged
-    f, J = run(s, pts, dd)
-    check_exact_oracle(s, pts, f, J, DD_TOL if dd else F64_TOL, dd=dd)
+    f, J = run(s, pts, prec)
+    check_exact_oracle(s, pts, f, J, tol(prec), dd=prec != "f64")
 
 
-@pytest.mark.parametrize("dd", [True, False], ids=["dd", "f64"])
-def test_gaussian_integers_bit_exact(dd):
+@pytest.mark.parametrize("prec", PRECS)
+def test_gaussian_integers_bit_exact(prec):
     rng = np.random.Generator(np.random.PCG64(103))
     n = 5
     polys = []
@@ -82,14 +82,14 @@ def test_gaussian_integers_bit_exact(dd):
     pts = np.zeros((n, P, 4))
     pts[..., 0] = rng.integers(-2, 3, size=(n, P))
     pts[..., 2] = rng.integers(-2, 3, size=(n, P))
-    f, J = run(s, pts, dd)
+    f, J = run(s, pts, prec)
     Fx, Jx = E.evaluate_dd(s, pts, range(P))
     assert np.array_equal(f, Fx)
     assert np.array_equal(J, Jx)
 
 
-@pytest.mark.parametrize("dd", [True, False], ids=["dd", "f64"])
-def test_worked_example_common_factor(dd):
+@pytest.mark.parametrize("prec", PRECS)
+def test_worked_example_common_factor(prec):
     """x1^3 x2^7 x3^2 (Section 3.1): common factor x1^2 x2^6 x3; the
     derivatives are 3 x1^2 x2^7 x3^2, 7 x1^3 x2^6 x3^2 and 2 x1^3 x2^7 x3."""
     s = synth.from_monomials(3, [[([0, 1, 2], [3, 7, 2])]], [[1.0, 0, 0, 0]])
@@ -97,7 +97,7 @@ def test_worked_example_common_factor(dd):
     pts[:, 0, 0] = [2, -1, 3]
     pts[:, 0, 2] = [1, 1, 0]
     pts[:, 1] = synth.points(104, 3, 1)[:, 0]
-    f, J = run(s, pts, dd)
+    f, J = run(s, pts, prec)
     x = [complex(2, 1), complex(-1, 1), complex(3, 0)]
     want_f = x[0] ** 3 * x[1] ** 7 * x[2] ** 2
     want_J = [3 * x[0] ** 2 * x[1] ** 7 * x[2] ** 2, 7 * x[0] ** 3 * x[1] ** 6 * x[2] ** 2,
@@ -106,11 +106,11 @@ def test_worked_example_common_factor(dd):
     for i in range(3):
         assert (J[0, i, 0, 0], J[0, i, 0, 2]) == (want_J[i].real, want_J[i].imag)
         assert J[0, i, 0, 1] == 0.0 and J[0, i, 0, 3] == 0.0
-    check_exact_oracle(s, pts, f, J, DD_TOL if dd else F64_TOL, dd=dd)
+    check_exact_oracle(s, pts, f, J, tol(prec), dd=prec != "f64")
 
 
-@pytest.mark.parametrize("dd", [True, False], ids=["dd", "f64"])
-def test_edge_cases_k0_k1_k2_absent_variables(dd):
+@pytest.mark.parametrize("prec", PRECS)
+def test_edge_cases_k0_k1_k2_absent_variables(prec):
     # constant terms, k = 1 and k = 2 monomials, a variable (x4) in no monomial,
     # a polynomial with only a constant, an empty polynomial
     polys = [
@@ -123,24 +123,24 @@ def test_edge_cases_k0_k1_k2_absent_variables(dd):
     M = sum(len(p) for p in polys)
     s = synth.from_monomials(5, polys, synth.random_cdd(np.random.Generator(np.random.PCG64(105)), M))
     pts = synth.points(106, 5, 19)
-    f, J = run(s, pts, dd)
-    check_exact_oracle(s, pts, f, J, DD_TOL if dd else F64_TOL, dd=dd)
+    f, J = run(s, pts, prec)
+    check_exact_oracle(s, pts, f, J, tol(prec), dd=prec != "f64")
     assert np.all(J[:, 4] == 0.0)              # x4 occurs nowhere
     assert not np.any(np.signbit(J[:, 4]))      # written as +0.0
     assert np.all(J[2] == 0.0) and np.all(J[3] == 0.0)
     assert np.all(f[3] == 0.0)
 
 
-@pytest.mark.parametrize("dd", [True, False], ids=["dd", "f64"])
-def test_one_variable_and_one_point(dd):
+@pytest.mark.parametrize("prec", PRECS)
+def test_one_variable_and_one_point(prec):
     s = synth.from_monomials(1, [[([0], [5]), ([], [])]], [[0.5, 0, -2, 0], [1, 0, 0, 0]])
     pts = synth.points(107, 1, 1)
-    f, J = run(s, pts, dd)
-    check_exact_oracle(s, pts, f, J, DD_TOL if dd else F64_TOL, dd=dd)
+    f, J = run(s, pts, prec)
+    check_exact_oracle(s, pts, f, J, tol(prec), dd=prec != "f64")
 
 
-@pytest.mark.parametrize("dd", [True, False], ids=["dd", "f64"])
-def test_largest_exponent_and_variable_index(dd):
+@pytest.mark.parametrize("prec", PRECS)
+def test_largest_exponent_and_variable_index(prec):
     """Exponent 256 (the largest the paper's byte encoding allows) and the
     variable index n-1 = 65534 (the largest position)."""
     n = 65535
@@ -150,16 +150,16 @@ def test_largest_exponent_and_variable_index(dd):
     pts = np.zeros((n, P, 4))
     used = [0, 1000, n - 2, n - 1]
     pts[used] = synth.points(110, len(used), P)  # unit circle: |x|^256 stays near 1
-    f, J = run(s, pts, dd)
-    s_ref, p_ref = (s, pts) if dd else fp64_inputs(s, pts)
-    tol = DD_TOL if dd else F64_TOL
+    f, J = run(s, pts, prec)
+    s_ref, p_ref = (s, pts) if prec != "f64" else fp64_inputs(s, pts)
+    tl = tol(prec)
     for q in range(P):
         fx, Jx = E.evaluate_point(s_ref, p_ref, q)
         Sf, SJ = E.scales_point(s_ref, p_ref, q)
         for p in range(2):
-            assert E.normwise_error(f[p, q], fx[p], Sf[p]) <= tol
+            assert E.normwise_error(f[p, q], fx[p], Sf[p]) <= tl
             for i, v in Jx[p].items():
-                assert E.normwise_error(J[p, i, q], v, SJ[p][i]) <= tol
+                assert E.normwise_error(J[p, i, q], v, SJ[p][i]) <= tl
     mask = np.ones(n, dtype=bool)
     mask[[0, 1000, n - 1]] = False
     assert np.all(J[0][mask] == 0.0)
@@ -261,21 +261,22 @@ def test_cuda_graph_replay_matches_eager():
 # the five workloads
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("dd", [True, False], ids=["dd", "f64"])
-def test_config1_tiny(dd):
+@pytest.mark.parametrize("prec", PRECS)
+def test_config1_tiny(prec):
     s, pts = synth.config(1)
-    f, J = run(s, pts, dd)
-    check_exact_oracle(s, pts, f, J, DD_TOL if dd else F64_TOL, dd=dd)
+    f, J = run(s, pts, prec)
+    check_exact_oracle(s, pts, f, J, tol(prec), dd=prec != "f64")
 
 
-def test_config2_full_batch_dd():
+@pytest.mark.parametrize("prec", ["dd", "ddint"])
+def test_config2_full_batch_dd(prec):
     """The benchmark workload at full size (1024 points): every output
     against the C double-double oracle (itself within 1e-30 of exact), and
     sampled points against the exact oracle."""
     import oracle
 
     s, pts = synth.config(2)
-    f, J = run(s, pts, True)
+    f, J = run(s, pts, prec)
     Fo, Jo = oracle.dd_eval(s, pts, threads=0)
     Sf, SJ = scales(s, pts)
     assert normwise_vs(f, Fo, Sf) <= DD_TOL
@@ -290,19 +291,20 @@ def test_config2_full_batch_f64():
     check_exact_oracle(s64, p64, f, J, F64_TOL, points_idx=[0, 700, 1023], polys=[0, 31])
 
 
-@pytest.mark.parametrize("dd", [True, False], ids=["dd", "f64"])
-def test_config3_sampled(dd):
+@pytest.mark.parametrize("prec", PRECS)
+def test_config3_sampled(prec):
     s, pts = synth.config(3)
-    f, J = run(s, pts, dd)
-    check_exact_oracle(s, pts, f, J, DD_TOL if dd else F64_TOL, points_idx=[0, 4095], polys=[0, 63], dd=dd)
+    f, J = run(s, pts, prec)
+    check_exact_oracle(s, pts, f, J, tol(prec), points_idx=[0, 4095], polys=[0, 63], dd=prec != "f64")
 
 
-def test_config3_homogeneous_euler_identity():
+@pytest.mark.parametrize("prec", ["dd", "ddint"])
+def test_config3_homogeneous_euler_identity(prec):
     """sum_i x_i df_p/dx_i = 24 f_p on the homogeneous variant (degree 24),
     checked exactly on sampled points; and the outputs against the exact
     oracle there."""
     s, pts = synth.config(3, homogeneous=True)
-    f, J = run(s, pts, True)
+    f, J = run(s, pts, prec)
     from fractions import Fraction
 
     for q in (0, 2047, 4095):
@@ -323,14 +325,15 @@ def test_config3_homogeneous_euler_identity():
     check_exact_oracle(s, pts, f, J, DD_TOL, points_idx=[1], polys=[5])
 
 
-def test_config4_ragged_batch():
+@pytest.mark.parametrize("prec", ["dd", "ddint"])
+def test_config4_ragged_batch(prec):
     import torch
 
     import oracle
     import paper_1201_0499_gb300 as pkg
 
     systems, pts = synth.config(4)
-    ev = pkg.PolyEvalMany(systems, [p.shape[1] for p in pts], pkg.PE_DD)
+    ev = pkg.PolyEvalMany(systems, [p.shape[1] for p in pts], pkg.PE_DD if prec == "dd" else pkg.PE_DD_INT)
     fs, Js = ev.eval([to_device(p) for p in pts])
     torch.cuda.synchronize()
     assert pkg.polyeval_status(ev.handle) == pkg.PE_OK
@@ -353,16 +356,16 @@ def test_config4_ragged_batch():
         check_exact_oracle(s, x, f, J, DD_TOL, points_idx=[q], polys=[p])
 
 
-@pytest.mark.parametrize("dd", [True, False], ids=["dd", "f64"])
-def test_config5_large_sampled(dd):
+@pytest.mark.parametrize("prec", PRECS)
+def test_config5_large_sampled(prec):
     import torch
 
     import oracle
 
     s, pts = synth.config(5)
-    f, J = run(s, pts, dd)
-    check_exact_oracle(s, pts, f, J, DD_TOL if dd else F64_TOL, points_idx=[16383], polys=[127], dd=dd)
-    if dd:
+    f, J = run(s, pts, prec)
+    check_exact_oracle(s, pts, f, J, tol(prec), points_idx=[16383], polys=[127], dd=prec != "f64")
+    if prec != "f64":
         sub = [0, 8191, 16383]
         Fo, Jo = oracle.dd_eval(s, pts[:, sub].copy(), threads=0)
         Sf, SJ = scales(s, pts[:, sub])
