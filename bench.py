@@ -198,6 +198,88 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+class Workload:
+    """The batch one step evaluates, in double-double and in double, with its
+    device buffers and pinned host buffers."""
+
+    def __init__(self, cfg, rank, dev, primary):
+        import torch
+
+        import paper_1201_0499_gb300 as pkg
+
+        self.pkg, self.torch, self.dev, self.cfg = pkg, torch, dev, cfg
+        prim = pkg.PE_DD_INT if primary == "ddint" else pkg.PE_DD
+        if cfg == 4:
+            systems, pts = synth.config(4)
+            self.text = synth.CONFIG_TEXT[4] + ", one launch"
+            self.many = {True: pkg.PolyEvalMany(systems, [p.shape[1] for p in pts], prim),
+                         False: pkg.PolyEvalMany([s.as_fp64() for s in systems], [p.shape[1] for p in pts],
+                                                 pkg.PE_F64)}
+            self.points = sum(p.shape[1] for p in pts)
+            self.bufs = {}
+            for dd, ev in self.many.items():
+                b = ev.buffers(dev)
+                ev.pack_points([torch.from_numpy(p if dd else np.ascontiguousarray(p[..., [0, 2]])) for p in pts], b[0])
+                self.bufs[dd] = b
+            self.host = [t.cpu().pin_memory() for t in self.bufs[True]]
+            self.system, self.pts = systems, pts
+        else:
+            if cfg == CONFIG_INDEX:
+                system, _ = synth.config(cfg, n_points=1)
+                P = 1024
+                pts = synth.points(rank_points_seed(rank), system.n_vars, P)
+                self.text = WORKLOAD
+            else:
+                system, pts = synth.config(cfg)
+                P = pts.shape[1]
+                self.text = synth.CONFIG_TEXT[cfg]
+            n, N = system.n_vars, system.n_polys
+            self.system, self.pts, self.points = system, pts, P
+            self.single = {True: pkg.PolyEval(system, prim, max_points=P),
+                           False: pkg.PolyEval(system.as_fp64(), pkg.PE_F64, max_points=P)}
+            self.bufs = {}
+            for dd in (True, False):
+                c = 4 if dd else 2
+                x = torch.from_numpy(pts if dd else np.ascontiguousarray(pts[..., [0, 2]])).to(dev)
+                self.bufs[dd] = (x, torch.empty((N, P, c), dtype=torch.float64, device=dev),
+                                 torch.empty((N, n, P, c), dtype=torch.float64, device=dev))
+            self.host = [torch.from_numpy(pts).pin_memory(), torch.empty((N, P, 4), dtype=torch.float64).pin_memory(),
+                         torch.empty((N, n, P, 4), dtype=torch.float64).pin_memory()]
+        self.h2d_bytes = int(self.host[0].numel() * 8)
+        self.d2h_bytes = int((self.host[1].numel() + self.host[2].numel()) * 8)
+
+    def handle(self, dd):
+        return self.many[dd].handle if self.cfg == 4 else self.single[dd].handle
+
+    def eval(self, dd):
+        x, f, J = self.bufs[dd]
+        if self.cfg == 4:
+            self.many[dd].eval_buffers(x, f, J)
+        else:
+            self.single[dd].eval(x, f, J)
+
+    def eval_host(self):
+        """Host points in, host f and J out, through the public entry points."""
+        if self.cfg == 4:
+            x, f, J = self.bufs[True]
+            x.copy_(self.host[0], non_blocking=True)
+            self.many[True].eval_buffers(x, f, J)
+            self.host[1].copy_(f, non_blocking=True)
+            self.host[2].copy_(J, non_blocking=True)
+            self.torch.cuda.current_stream().synchronize()
+        else:
+            hp, hf, hJ = self.host
+            self.pkg.polyeval_eval_host(self.single[True].handle, hp, self.points, hf, hJ,
+                                        self.torch.cuda.current_stream())
+
+    def cost_per_launch(self):
+        """FP64 instructions and flops of one main-kernel launch."""
+        if self.cfg == 4:
+            return self.many[True].cost()  # a batch handle reports whole-evaluation totals
+        ops, flops = self.single[True].cost()
+        return ops * self.points, flops * self.points
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -205,6 +287,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="dd", choices=["dd", "ddint"],
+                    help="dd: double-double on the FP64 pipe; ddint: products in 128-bit integer block "
+                         "floating point, sums in double-double (same inputs, outputs and accuracy bar)")
+    ap.add_argument("--config", type=int, default=CONFIG_INDEX, choices=[2, 3, 4, 5],
+                    help="workload (default 2, the benchmark workload; 3, 4, 5: the larger and ragged ones)")
     args = ap.parse_args()
     rank, world, local = env_dist()
     dist = None
@@ -224,90 +311,77 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    system, _ = synth.config(CONFIG_INDEX, n_points=1)
-    P = 1024
-    pts = synth.points(rank_points_seed(rank), system.n_vars, P)
-    n, N = system.n_vars, system.n_polys
-    ev = pkg.PolyEval(system, pkg.PE_DD, max_points=P)
-    x = torch.from_numpy(pts).to(dev)
-    f = torch.empty((N, P, 4), dtype=torch.float64, device=dev)
-    J = torch.empty((N, n, P, 4), dtype=torch.float64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    wl = Workload(args.config, rank, dev, args.precision)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def timed_loop(evaluator, xin, fo, Jo, steps):
+    def timed_loop(dd, steps):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         for i in range(steps):
             flush.zero_()  # L2 flush between timed steps (outside the step's events)
             starts[i].record(stream)
-            evaluator.eval(xin, fo, Jo)
+            wl.eval(dd)
             stops[i].record(stream)
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in zip(starts, stops))
 
     for _ in range(args.warmup):
-        ev.eval(x, f, J)
+        wl.eval(True)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    pkg.polyeval_timing(ev.handle, True)
+    pkg.polyeval_timing(wl.handle(True), True)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.time()
-    total_ms = timed_loop(ev, x, f, J, args.steps)
+    total_ms = timed_loop(True, args.steps)
     t_wall1 = time.time()
     if dist is not None:
         dist.barrier()
-    kern_ms, launches = pkg.polyeval_timing_read(ev.handle)
-    pkg.polyeval_timing(ev.handle, False)
+    kern_ms, launches, kernels = pkg.polyeval_timing_read(wl.handle(True))
+    pkg.polyeval_timing(wl.handle(True), False)
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
-    assert ev.status() == pkg.PE_OK
+    assert pkg.polyeval_status(wl.handle(True)) == pkg.PE_OK
 
+    P = wl.points
     ms_per_step = max_over_ranks(total_ms / args.steps, dist)
     value = job_throughput(world, P, ms_per_step)
 
     # roofline of the main (monomial) kernel: FP64 pipe bound
-    ops_pp, flops_pp = ev.cost()
+    ops_launch, flops_launch = wl.cost_per_launch()
     kern_avg_ms = kern_ms / max(launches, 1)
-    achieved_tflops = flops_pp * P / (kern_avg_ms * 1e-3) / 1e12
+    achieved_tflops = flops_launch / (kern_avg_ms * 1e-3) / 1e12
     peaks = peaks_file()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_nominal = SMS * DFMA_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
     fma_rate, probe_mhz = pkg.polyeval_fp64_peak(stream)
     peak_probe = 2 * fma_rate / 1e12
-    issue_rate = ops_pp * P / (kern_avg_ms * 1e-3)
+    issue_rate = ops_launch / (kern_avg_ms * 1e-3)
 
     # complex double path on the same workload, same harness
-    ev64 = pkg.PolyEval(system.as_fp64(), pkg.PE_F64, max_points=P)
-    x64 = torch.from_numpy(np.ascontiguousarray(pts[..., [0, 2]])).to(dev)
-    f64 = torch.empty((N, P, 2), dtype=torch.float64, device=dev)
-    J64 = torch.empty((N, n, P, 2), dtype=torch.float64, device=dev)
     for _ in range(args.warmup):
-        ev64.eval(x64, f64, J64)
-    k64 = max(args.steps, 10)
-    ms64 = timed_loop(ev64, x64, f64, J64, k64) / k64
+        wl.eval(False)
+    k64 = max(args.steps, 10) if args.config == CONFIG_INDEX else args.steps
+    ms64 = timed_loop(False, k64) / k64
 
-    # end to end through the host entry point: pinned host in, pinned host out
-    hp = torch.from_numpy(pts).pin_memory()
-    hf = torch.empty((N, P, 4), dtype=torch.float64).pin_memory()
-    hJ = torch.empty((N, n, P, 4), dtype=torch.float64).pin_memory()
+    # end to end through the public API: pinned host in, pinned host out
     for _ in range(max(args.warmup, 1)):
-        pkg.polyeval_eval_host(ev.handle, hp, P, hf, hJ, stream)
+        wl.eval_host()
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        pkg.polyeval_eval_host(ev.handle, hp, P, hf, hJ, stream)
+        wl.eval_host()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample = cpu_oracle_rate(system, pts, seconds=10.0)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == CONFIG_INDEX:
+        rate, cores, sample = cpu_oracle_rate(wl.system, wl.pts, seconds=10.0)
         cpu = {"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -324,15 +398,20 @@ def main():
             "vs_baseline": None,
             "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "points_per_gpu": P, "precision": "complex double-double",
+            "config": {"workload": wl.text, "points_per_gpu": P,
+                       "precision": ("complex double-double" if args.precision == "dd" else
+                                     "complex double-double in/out, products in 128-bit integer block floating point"),
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
-                       "launch": "powers kernel + persistent monomial kernel per step"},
+                       "launch": f"{kernels // max(args.steps, 1)} kernels per step (power table, monomial "
+                                 "kernel, combine of monomial chunks when the call has few items)"},
             "e2e": {"value": job_throughput(world, P, e2e_ms), "unit": "evals/s",
-                    "h2d_bytes_per_step": int(hp.numel() * 8), "d2h_bytes_per_step": int((hf.numel() + hJ.numel()) * 8)},
-            "gpu_launches": 2 * args.steps,
+                    "h2d_bytes_per_step": wl.h2d_bytes, "d2h_bytes_per_step": wl.d2h_bytes},
+            "gpu_launches": kernels,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_nominal, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak_nominal, "traffic": MAIN_KERNEL_DRAM_BYTES,
-                         "kernel": "main_kernel<ArithDD>", "kernel_ms": kern_avg_ms,
+                         "frac": achieved_tflops / peak_nominal,
+                         "traffic": MAIN_KERNEL_DRAM_BYTES if args.config == CONFIG_INDEX else None,
+                         "kernel": "main_kernel<ArithDD>" if args.precision == "dd" else "main_wide",
+                         "kernel_ms": kern_avg_ms,
                          "peak_basis": f"nominal: {SMS} SMs x {DFMA_PER_SM_CLK} FP64 FMA/clk x 2 flops x {sm_max:.0f} MHz",
                          "peak_probe": peak_probe, "frac_of_probe": achieved_tflops / peak_probe,
                          "probe_sm_mhz": probe_mhz,

@@ -153,9 +153,12 @@ PE_API int polyeval_create(const pe_system *sys, int precision, uint32_t flags, 
  *   out_J   device, [n_polys][n_vars][P] of the same element type
  *   stream  cudaStream_t the work is queued on
  * Allocates nothing, synchronises nothing, and only queues kernels and one
- * 4-byte cudaMemsetAsync, so a call can be captured in a CUDA graph.  Calls
- * on one handle must not overlap on the GPU (they share the power table and
- * the work counter).  Errors: PE_EINVAL (null handle/pointer with P > 0),
+ * 4-byte cudaMemsetAsync, so a call can be captured in a CUDA graph.  When
+ * the call has few (polynomial, tile of 16 points) work items, each
+ * polynomial's monomials are split into up to 8 chunks whose partial sums go
+ * to handle-owned scratch (at most 256 MiB, sized at create) and are added
+ * by a final kernel.  Calls on one handle must not overlap on the GPU (they
+ * share the power table, the scratch and the work counter).  Errors: PE_EINVAL (null handle/pointer with P > 0),
  * PE_ERANGE (P > max_points), PE_ECUDA (launch failure).
  */
 PE_API int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream);
@@ -217,11 +220,13 @@ PE_API int polyeval_cost(const polyeval_t *h, double *fp64_ops, double *fp64_flo
  * each following eval call records a pair of CUDA events on its stream
  * around the main kernel (at most 256 pairs are kept).  polyeval_timing_read
  * waits for the recorded events, returns the summed kernel time in
- * milliseconds and the number of timed launches, and starts a new count.
- * Returns PE_ERANGE if launches beyond the 256 kept pairs went untimed.
+ * milliseconds, the number of timed launches and the number of kernels the
+ * eval calls queued (power table, main kernel, combine passes), and starts a
+ * new count.  Returns PE_ERANGE if launches beyond the 256 kept pairs went
+ * untimed.  Any output pointer may be NULL.
  */
 PE_API int polyeval_timing(polyeval_t *h, int enable);
-PE_API int polyeval_timing_read(polyeval_t *h, double *total_ms, int64_t *launches);
+PE_API int polyeval_timing_read(polyeval_t *h, double *total_ms, int64_t *launches, int64_t *kernels);
 
 /*
  * Read and clear the device status word (synchronises the device).

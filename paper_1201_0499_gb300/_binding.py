@@ -80,7 +80,7 @@ def load_library(path: Optional[str] = None):
         "polyeval_eval_many": ([P, P, P, P, P], ctypes.c_int),
         "polyeval_cost": ([P, D, D], ctypes.c_int),
         "polyeval_timing": ([P, ctypes.c_int], ctypes.c_int),
-        "polyeval_timing_read": ([P, D, ctypes.POINTER(I64)], ctypes.c_int),
+        "polyeval_timing_read": ([P, D, ctypes.POINTER(I64), ctypes.POINTER(I64)], ctypes.c_int),
         "polyeval_status": ([P], ctypes.c_int),
         "polyeval_destroy": ([P], None),
         "polyeval_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -209,9 +209,11 @@ def polyeval_timing(h: int, enable: bool) -> None:
 
 
 def polyeval_timing_read(h: int):
-    ms, n = ctypes.c_double(), ctypes.c_int64()
-    _check(load_library().polyeval_timing_read(h, ctypes.byref(ms), ctypes.byref(n)), "polyeval_timing_read")
-    return ms.value, n.value
+    """(summed main-kernel ms, timed launches, kernels queued) since polyeval_timing."""
+    ms, n, k = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().polyeval_timing_read(h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)),
+           "polyeval_timing_read")
+    return ms.value, n.value, k.value
 
 
 def polyeval_status(h: int) -> int:

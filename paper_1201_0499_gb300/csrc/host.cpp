@@ -19,6 +19,11 @@ using pe::SysDesc;
 namespace {
 
 constexpr int kMaxTimingEvents = 256;
+// Splitting a polynomial's monomials into chunks (single-system calls with
+// few (polynomial, tile) items): at most kMaxChunks chunks, partial results
+// in at most kScratchBudget bytes of handle-owned scratch.
+constexpr int kMaxChunks = 8;
+constexpr size_t kScratchBudget = size_t{256} << 20;
 
 struct DeviceBuf {
   void *p = nullptr;
@@ -71,10 +76,12 @@ struct polyeval {
   // device memory
   DeviceBuf poly_ptr, mono_ptr, var, coef, coef_wide, poly_sys, sysd, perm, items, prefix, table, counter, status;
   DeviceBuf stage_pts, stage_f, stage_J;
+  DeviceBuf scratch;  // chunk partial results (single-system handles)
   // timing of the main kernel
   bool timing = false;
   cudaEvent_t ev[2 * kMaxTimingEvents] = {};
   int ev_used = 0, ev_dropped = 0;
+  int64_t kernels_launched = 0;  // kernels queued by evals since timing was enabled
   ~polyeval() {
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
@@ -94,9 +101,18 @@ int64_t table_levels(const polyeval *h, int emax) {
 size_t table_entry_bytes(const polyeval *h) { return h->wide ? pe::kWideBytes : elem_doubles(h) * sizeof(double); }
 
 // Launch the power-table kernel of the handle's precision.
-int run_powers(const polyeval *h, const pe::PowerParams &pp, cudaStream_t s) {
+int run_powers(polyeval *h, const pe::PowerParams &pp, cudaStream_t s) {
   const cudaError_t e = h->wide ? pe::launch_powers_wide(pp, s) : pe::launch_powers(h->dd, pp, s);
-  return e == cudaSuccess ? PE_OK : PE_ECUDA;
+  if (e != cudaSuccess) return PE_ECUDA;
+  if (pp.total > 0) h->kernels_launched++;
+  return PE_OK;
+}
+
+// Bytes of one copy of f and J of a single-system call at P points.
+size_t outputs_bytes(const polyeval *h, int64_t P) {
+  const SysDesc &d = h->sys[0];
+  return static_cast<size_t>(elem_doubles(h)) * sizeof(double) * static_cast<size_t>(P) *
+         (static_cast<size_t>(d.N) + static_cast<size_t>(d.N) * d.n);
 }
 
 // FP64 instructions and flops per point for one monomial (k variables, n2 of
@@ -318,6 +334,7 @@ int run_main(polyeval *h, const pe::MainParams &mp, cudaStream_t s) {
   const cudaError_t le = h->wide ? pe::launch_main_wide(mp, sh.warps, sh.smem, sh.grid, s)
                                  : pe::launch_main(h->dd, mp, sh.warps, sh.smem, sh.grid, s);
   if (le != cudaSuccess) return PE_ECUDA;
+  h->kernels_launched++;
   if (e1 && cudaEventRecord(e1, s) != cudaSuccess) return PE_ECUDA;
   return PE_OK;
 }
@@ -373,6 +390,14 @@ int polyeval_create(const pe_system *sys, int precision, uint32_t flags, int64_t
     if ((rc = finish_handle(h, c)) != PE_OK || (rc = h->perm.upload(perm)) != PE_OK) {
       delete h;
       return rc;
+    }
+    {
+      const size_t per_chunk = outputs_bytes(h, max_points);
+      const size_t want = std::min(static_cast<size_t>(kMaxChunks - 1) * per_chunk, kScratchBudget);
+      if (per_chunk > 0 && want >= per_chunk && (rc = h->scratch.alloc(want)) != PE_OK) {
+        delete h;
+        return rc;
+      }
     }
     const int64_t levels = table_levels(h, d.emax);
     if (levels > 0) {
@@ -524,8 +549,31 @@ int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, voi
   mp.out_J = static_cast<double *>(out_J);
   mp.single_P = static_cast<int32_t>(P);
   mp.single_T = static_cast<int32_t>((P + pe::kPointsPerWarp - 1) / pe::kPointsPerWarp);
-  mp.n_items = static_cast<int64_t>(d.N) * mp.single_T;
-  return run_main(h, mp, s);
+  const int64_t base = static_cast<int64_t>(d.N) * mp.single_T;
+  // Few (polynomial, tile) items: split each polynomial's monomials into
+  // chunks so that about one wave of resident warps has work.
+  int C = 1;
+  const int64_t capacity = static_cast<int64_t>(h->sms) * h->blocks_per_sm_1;
+  const size_t per_chunk = outputs_bytes(h, P);
+  if (base > 0 && per_chunk > 0) {
+    C = static_cast<int>(std::min<int64_t>(kMaxChunks, std::max<int64_t>(1, capacity / base)));
+    C = static_cast<int>(std::min<int64_t>(C, 1 + static_cast<int64_t>(h->scratch.bytes / per_chunk)));
+  }
+  const int64_t f_doubles = static_cast<int64_t>(elem_doubles(h)) * d.N * P;
+  const int64_t J_doubles = f_doubles * d.n;
+  mp.n_chunks = C;
+  mp.chunk_f_stride = f_doubles;
+  mp.chunk_J_stride = J_doubles;
+  mp.scratch_f = static_cast<double *>(h->scratch.p);
+  mp.scratch_J = C > 1 ? mp.scratch_f + static_cast<size_t>(C - 1) * f_doubles : nullptr;
+  mp.n_items = base * C;
+  int rc = run_main(h, mp, s);
+  if (rc != PE_OK || C == 1) return rc;
+  if (pe::launch_combine(h->dd, mp.out_f, mp.out_J, mp.scratch_f, mp.scratch_J, f_doubles, J_doubles, C, s) !=
+      cudaSuccess)
+    return PE_ECUDA;
+  h->kernels_launched += 2;  // f and J passes
+  return PE_OK;
 }
 
 int polyeval_eval_many(polyeval_t *h, const void *points, void *out_f, void *out_J, void *stream) {
@@ -550,6 +598,7 @@ int polyeval_eval_many(polyeval_t *h, const void *points, void *out_f, void *out
   mp.out_J = static_cast<double *>(out_J);
   mp.single_P = -1;
   mp.single_T = 0;
+  mp.n_chunks = 1;
   mp.n_items = h->n_items_batch;
   return run_main(h, mp, s);
 }
@@ -591,10 +640,11 @@ int polyeval_timing(polyeval_t *h, int enable) {
   h->timing = enable != 0;
   h->ev_used = 0;
   h->ev_dropped = 0;
+  h->kernels_launched = 0;
   return PE_OK;
 }
 
-int polyeval_timing_read(polyeval_t *h, double *total_ms, int64_t *launches) {
+int polyeval_timing_read(polyeval_t *h, double *total_ms, int64_t *launches, int64_t *kernels) {
   if (!h) return PE_EINVAL;
   double tot = 0.0;
   for (int i = 0; i < h->ev_used; i++) {
@@ -605,6 +655,8 @@ int polyeval_timing_read(polyeval_t *h, double *total_ms, int64_t *launches) {
   }
   if (total_ms) *total_ms = tot;
   if (launches) *launches = h->ev_used;
+  if (kernels) *kernels = h->kernels_launched;
+  h->kernels_launched = 0;
   const int dropped = h->ev_dropped;
   h->ev_used = 0;
   h->ev_dropped = 0;

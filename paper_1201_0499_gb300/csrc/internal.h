@@ -45,6 +45,11 @@ struct MainParams {
   int32_t single_T;         // tiles of a single-system call
   int32_t kslots;           // prefix-product slots per lane (max k - 1, at least 1)
   int32_t n_polys_total;
+  int32_t n_chunks;         // single handle: chunks per polynomial's monomials (>= 1)
+  int64_t chunk_f_stride;   // doubles between scratch copies of f
+  int64_t chunk_J_stride;   // doubles between scratch copies of J
+  double *scratch_f;        // chunk partial results 1 .. n_chunks-1
+  double *scratch_J;
   unsigned int *counter;    // work counter (zeroed before each launch)
   int *status;              // device status word
 };
@@ -69,6 +74,12 @@ cudaError_t launch_main(bool dd, const MainParams &p, int warps_per_block, size_
 cudaError_t main_occupancy(bool dd, int warps_per_block, size_t smem_bytes, int *blocks_per_sm);
 cudaError_t prepare_main(bool dd, size_t smem_bytes);
 cudaError_t fp64_peak_probe(cudaStream_t s, double *fma_per_s, double *sm_clock_mhz);
+
+// Adds the chunk partial results into the outputs and renormalises:
+// out[i] = out[i] + scratch_1[i] + ... + scratch_{C-1}[i] for the f and J
+// arrays of one system (elements of `doubles_per_elem` doubles).
+cudaError_t launch_combine(bool dd, double *out_f, double *out_J, const double *scratch_f, const double *scratch_J,
+                           int64_t f_doubles, int64_t J_doubles, int chunks, cudaStream_t s);
 
 // Integer-pipe evaluation (kernels_wide.cu): 128-bit block floating point
 // products, double-double sums.  Table entries and coefficients are 48 bytes.

@@ -1,0 +1,62 @@
+// Decoding of a work item of the main kernels (kernels.cu, kernels_wide.cu).
+//
+// A single-system call has N x T x C items: polynomial rank r (in decreasing
+// cost order), tile of 16 points, and chunk of the polynomial's monomials
+// (C = 1 unless the call has too few (polynomial, tile) pairs to fill the
+// GPU).  Chunk 0 writes f and J into the outputs; chunk c > 0 into scratch
+// copy c-1 of the same layout, which a combine kernel adds afterwards.  A
+// batch handle has one item per (polynomial, tile) from its item table.
+#pragma once
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace pe {
+
+struct Item {
+  int gp, tile, s, P;  // global polynomial, tile, system, points of the system
+  int t0, t1;          // monomial range
+  double *f_base;      // output (or scratch) base for f
+  double *J_base;      // output (or scratch) base for J
+};
+
+// Returns false (and flags the status word) for an inconsistent item.
+__device__ __forceinline__ bool decode_item(const MainParams &kp, unsigned item, int lane, Item &it) {
+  int chunk = 0;
+  if (kp.single_P >= 0) {
+    const unsigned C = static_cast<unsigned>(kp.n_chunks);
+    const unsigned rest = item / C;
+    chunk = static_cast<int>(item - rest * C);
+    const int r = static_cast<int>(rest) / kp.single_T;
+    it.tile = static_cast<int>(rest) - r * kp.single_T;
+    it.gp = kp.perm[r];
+    it.s = 0;
+    it.P = kp.single_P;
+  } else {
+    const int2 x = kp.items[item];
+    it.gp = x.x;
+    it.tile = x.y;
+    it.s = (x.x >= 0 && x.x < kp.n_polys_total) ? kp.poly_sys[x.x] : 0;
+    it.P = kp.sys[it.s].P;
+  }
+  if (it.gp < 0 || it.gp >= kp.n_polys_total || it.tile * kPointsPerWarp >= it.P) {
+    if (lane == 0) atomicOr(kp.status, 1);
+    return false;
+  }
+  int t0 = kp.poly_ptr[it.gp], t1 = kp.poly_ptr[it.gp + 1];
+  if (kp.n_chunks > 1) {
+    const long long m = t1 - t0;
+    const int a = t0 + static_cast<int>(m * chunk / kp.n_chunks);
+    const int b = t0 + static_cast<int>(m * (chunk + 1) / kp.n_chunks);
+    t0 = a;
+    t1 = b;
+  }
+  it.t0 = t0;
+  it.t1 = t1;
+  it.f_base = chunk == 0 ? kp.out_f : kp.scratch_f + static_cast<size_t>(chunk - 1) * kp.chunk_f_stride;
+  it.J_base = chunk == 0 ? kp.out_J : kp.scratch_J + static_cast<size_t>(chunk - 1) * kp.chunk_J_stride;
+  return true;
+}
+
+}  // namespace pe

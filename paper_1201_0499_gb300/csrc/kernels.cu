@@ -36,6 +36,7 @@
 
 #include "dd.cuh"
 #include "internal.h"
+#include "items.cuh"
 
 namespace pe {
 
@@ -173,7 +174,8 @@ __device__ __forceinline__ void accumulate(double *p, int c, bool valid, typenam
 // One work item: polynomial gp (global index) of system s at the points of
 // `tile`.  smem: this warp's prefix-product slots, [slot][lane].
 template <class A>
-__device__ void process_item(const MainParams &kp, int gp, int tile, int s, int P, typename A::V *smem, int lane) {
+__device__ void process_item(const MainParams &kp, const Item &it, typename A::V *smem, int lane) {
+  const int gp = it.gp, tile = it.tile, s = it.s, P = it.P;
   using V = typename A::V;
   using Full = typename A::Full;
   constexpr int KD = A::kDoubles;
@@ -188,7 +190,7 @@ __device__ void process_item(const MainParams &kp, int gp, int tile, int s, int 
   const int pl = gp - sd.poly0;
   const double *X = kp.points + static_cast<size_t>(sd.pt_off) * KD;
   const double *Tb = kp.table + static_cast<size_t>(sd.tab_off) * KD;
-  double *Jrow = kp.out_J + (static_cast<size_t>(sd.J_off) + static_cast<size_t>(pl) * n * Pz) * KD;
+  double *Jrow = it.J_base + (static_cast<size_t>(sd.J_off) + static_cast<size_t>(pl) * n * Pz) * KD;
 
   auto xel = [&](int v) { return X + (static_cast<size_t>(v) * Pz + qc) * KD; };
   auto tel = [&](int e, int v) { return Tb + ((static_cast<size_t>(e - 2) * n + v) * Pz + qc) * KD; };
@@ -198,7 +200,7 @@ __device__ void process_item(const MainParams &kp, int gp, int tile, int s, int 
     for (int v = 0; v < n; v++) A::store_comp(jel(v), c, A::zero());
 
   typename A::F f = A::f_zero();
-  const int t0 = kp.poly_ptr[gp], t1 = kp.poly_ptr[gp + 1];
+  const int t0 = it.t0, t1 = it.t1;
   for (int t = t0; t < t1; t++) {
     const int vb = kp.mono_ptr[t];
     const int k = kp.mono_ptr[t + 1] - vb;
@@ -238,7 +240,7 @@ __device__ void process_item(const MainParams &kp, int gp, int tile, int s, int 
     }
   }
   if (valid) {
-    A::store_comp(kp.out_f + (static_cast<size_t>(sd.f_off) + static_cast<size_t>(pl) * Pz + q) * KD, c,
+    A::store_comp(it.f_base + (static_cast<size_t>(sd.f_off) + static_cast<size_t>(pl) * Pz + q) * KD, c,
                   A::f_finish(f));
     for (int v = 0; v < n; v++) {
       double *p = jel(v);
@@ -257,25 +259,9 @@ __global__ void __launch_bounds__(kWarpsPerBlockMax * 32) main_kernel(const Main
     if (lane == 0) item = atomicAdd(kp.counter, 1u);
     item = __shfl_sync(kFull, item, 0);
     if (static_cast<int64_t>(item) >= kp.n_items) break;
-    int gp, tile, s, P;
-    if (kp.single_P >= 0) {
-      const int r = static_cast<int>(item) / kp.single_T;
-      tile = static_cast<int>(item) - r * kp.single_T;
-      gp = kp.perm[r];
-      s = 0;
-      P = kp.single_P;
-    } else {
-      const int2 it = kp.items[item];
-      gp = it.x;
-      tile = it.y;
-      s = (gp >= 0 && gp < kp.n_polys_total) ? kp.poly_sys[gp] : 0;
-      P = kp.sys[s].P;
-    }
-    if (gp < 0 || gp >= kp.n_polys_total || tile * kPointsPerWarp >= P) {
-      if (lane == 0) atomicOr(kp.status, 1);
-      continue;
-    }
-    process_item<A>(kp, gp, tile, s, P, smem, lane);
+    Item it;
+    if (!decode_item(kp, item, lane, it)) continue;
+    process_item<A>(kp, it, smem, lane);
   }
 }
 
@@ -320,6 +306,40 @@ __global__ void powers_kernel(const PowerParams pp) {
       A::store_full(entry(e), A::cmul(hi, lo));
     }
   }
+}
+
+// out[i] += sum of the chunk partials, renormalised (one component per thread).
+template <class A>
+__global__ void combine_kernel(double *out, const double *scratch, int64_t comps, int64_t stride, int chunks) {
+  constexpr int CD = A::kDoubles / 2;  // doubles per component
+  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < comps; i += step) {
+    typename A::V acc = A::load_comp(out + i * CD, 0);
+    for (int c = 1; c < chunks; c++) acc = A::add(acc, A::load_comp(scratch + (c - 1) * stride + i * CD, 0));
+    A::store_comp(out + i * CD, 0, A::finish(acc));
+  }
+}
+
+cudaError_t launch_combine(bool dd, double *out_f, double *out_J, const double *scratch_f, const double *scratch_J,
+                           int64_t f_doubles, int64_t J_doubles, int chunks, cudaStream_t s) {
+  if (chunks <= 1) return cudaSuccess;
+  const int threads = 256;
+  for (int pass = 0; pass < 2; pass++) {
+    double *out = pass ? out_J : out_f;
+    const double *scr = pass ? scratch_J : scratch_f;
+    const int64_t doubles = pass ? J_doubles : f_doubles;
+    const int64_t comps = dd ? doubles / 2 : doubles;
+    if (comps <= 0) continue;
+    int64_t blocks = (comps + threads - 1) / threads;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (dd)
+      combine_kernel<ArithDD><<<static_cast<unsigned>(blocks), threads, 0, s>>>(out, scr, comps, doubles, chunks);
+    else
+      combine_kernel<ArithF64><<<static_cast<unsigned>(blocks), threads, 0, s>>>(out, scr, comps, doubles, chunks);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_powers(bool dd, const PowerParams &p, cudaStream_t s) {

@@ -19,6 +19,7 @@
 
 #include "dd.cuh"
 #include "internal.h"
+#include "items.cuh"
 #include "wide.cuh"
 
 namespace pe {
@@ -99,7 +100,8 @@ __device__ __forceinline__ void accumulate_dd(double *p, int c, bool valid, dd x
   if (valid) reinterpret_cast<double2 *>(p)[c] = make_double2(s.h, s.l);
 }
 
-__device__ void process_item_wide(const MainParams &kp, int gp, int tile, int s, int P, uint32_t *slots, int lane) {
+__device__ void process_item_wide(const MainParams &kp, const Item &it, uint32_t *slots, int lane) {
+  const int gp = it.gp, tile = it.tile, s = it.s, P = it.P;
   const SysDesc sd = kp.sys[s];
   const int n = sd.n;
   const int q = tile * kPointsPerWarp + (lane >> 1);
@@ -110,7 +112,7 @@ __device__ void process_item_wide(const MainParams &kp, int gp, int tile, int s,
   const int pl = gp - sd.poly0;
   const uint32_t *Tb = reinterpret_cast<const uint32_t *>(kp.table) + static_cast<size_t>(sd.tab_off) * kWideWords;
   const uint32_t *coef = reinterpret_cast<const uint32_t *>(kp.coef);
-  double *Jrow = kp.out_J + (static_cast<size_t>(sd.J_off) + static_cast<size_t>(pl) * n * Pz) * 4;
+  double *Jrow = it.J_base + (static_cast<size_t>(sd.J_off) + static_cast<size_t>(pl) * n * Pz) * 4;
 
   auto tel = [&](int e, int v) { return Tb + ((static_cast<size_t>(e - 1) * n + v) * Pz + qc) * kWideWords; };
   auto jel = [&](int v) { return Jrow + (static_cast<size_t>(v) * Pz + qc) * 4; };
@@ -119,7 +121,7 @@ __device__ void process_item_wide(const MainParams &kp, int gp, int tile, int s,
     for (int v = 0; v < n; v++) reinterpret_cast<double2 *>(jel(v))[c] = make_double2(0.0, 0.0);
 
   dd f{0.0, 0.0};
-  const int t0 = kp.poly_ptr[gp], t1 = kp.poly_ptr[gp + 1];
+  const int t0 = it.t0, t1 = it.t1;
   for (int t = t0; t < t1; t++) {
     const int vb = kp.mono_ptr[t];
     const int k = kp.mono_ptr[t + 1] - vb;
@@ -159,7 +161,7 @@ __device__ void process_item_wide(const MainParams &kp, int gp, int tile, int s,
   }
   if (valid) {
     const dd fo = normalize(f);
-    reinterpret_cast<double2 *>(kp.out_f + (static_cast<size_t>(sd.f_off) + static_cast<size_t>(pl) * Pz + q) * 4)[c] =
+    reinterpret_cast<double2 *>(it.f_base + (static_cast<size_t>(sd.f_off) + static_cast<size_t>(pl) * Pz + q) * 4)[c] =
         make_double2(fo.h, fo.l);
     for (int v = 0; v < n; v++) {
       double2 *p = reinterpret_cast<double2 *>(jel(v)) + c;
@@ -179,25 +181,9 @@ __global__ void __launch_bounds__(kWarpsPerBlockMax * 32) main_wide(const MainPa
     if (lane == 0) item = atomicAdd(kp.counter, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (static_cast<int64_t>(item) >= kp.n_items) break;
-    int gp, tile, s, P;
-    if (kp.single_P >= 0) {
-      const int r = static_cast<int>(item) / kp.single_T;
-      tile = static_cast<int>(item) - r * kp.single_T;
-      gp = kp.perm[r];
-      s = 0;
-      P = kp.single_P;
-    } else {
-      const int2 it = kp.items[item];
-      gp = it.x;
-      tile = it.y;
-      s = (gp >= 0 && gp < kp.n_polys_total) ? kp.poly_sys[gp] : 0;
-      P = kp.sys[s].P;
-    }
-    if (gp < 0 || gp >= kp.n_polys_total || tile * kPointsPerWarp >= P) {
-      if (lane == 0) atomicOr(kp.status, 1);
-      continue;
-    }
-    process_item_wide(kp, gp, tile, s, P, slots, lane);
+    Item it;
+    if (!decode_item(kp, item, lane, it)) continue;
+    process_item_wide(kp, it, slots, lane);
   }
 }
 
