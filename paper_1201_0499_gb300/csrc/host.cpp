@@ -24,6 +24,9 @@ constexpr int kMaxTimingEvents = 256;
 // in at most kScratchBudget bytes of handle-owned scratch.
 constexpr int kMaxChunks = 8;
 constexpr size_t kScratchBudget = size_t{256} << 20;
+// Integer path: above this many prefix slots per lane a warp's slots no longer
+// leave room for 16 warps per SM, and only every second slot is stored.
+constexpr int kWideSlotsFull = 20;
 
 struct DeviceBuf {
   void *p = nullptr;
@@ -65,6 +68,7 @@ struct polyeval {
   std::vector<SysDesc> sys;
   int32_t n_polys_total = 0;
   int32_t kmax = 0, kslots = 1;
+  int32_t slot_stride = 1;  // integer path: keep every slot_stride-th forward product
   int warps_per_block = pe::kWarpsPerBlockMax;
   size_t smem_bytes = 0;
   int blocks_per_sm = 1, sms = 1;
@@ -240,6 +244,12 @@ int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, b
 int finish_handle(polyeval *h, Compiled &c) {
   h->kmax = c.kmax;
   h->kslots = std::max(c.kmax - 1, 1);
+  if (h->wide && h->kslots > kWideSlotsFull) {
+    // keep every second forward product (the others are recomputed in the
+    // backward pass) so that enough warps fit in shared memory
+    h->slot_stride = 2;
+    h->kslots = (h->kslots + 1) / 2;
+  }
   h->n_polys_total = static_cast<int32_t>(c.poly_sys.size());
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PE_ECUDA;
@@ -310,6 +320,7 @@ pe::MainParams main_params(const polyeval *h) {
   p.items = static_cast<const int2 *>(h->items.p);
   p.table = static_cast<const double *>(h->table.p);
   p.kslots = h->kslots;
+  p.slot_stride = h->slot_stride;
   p.n_polys_total = h->n_polys_total;
   p.counter = static_cast<unsigned *>(h->counter.p);
   p.status = static_cast<int *>(h->status.p);

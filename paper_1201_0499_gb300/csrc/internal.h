@@ -44,6 +44,7 @@ struct MainParams {
   int32_t single_P;         // >= 0: single-system handle evaluated at single_P points
   int32_t single_T;         // tiles of a single-system call
   int32_t kslots;           // prefix-product slots per lane (max k - 1, at least 1)
+  int32_t slot_stride;      // integer path: every slot_stride-th forward product is kept
   int32_t n_polys_total;
   int32_t n_chunks;         // single handle: chunks per polynomial's monomials (>= 1)
   int64_t chunk_f_stride;   // doubles between scratch copies of f
@@ -84,7 +85,7 @@ cudaError_t launch_combine(bool dd, double *out_f, double *out_J, const double *
 // Integer-pipe evaluation (kernels_wide.cu): 128-bit block floating point
 // products, double-double sums.  Table entries and coefficients are 48 bytes.
 constexpr int kWideBytes = 48;
-constexpr int kWideSlotBytes = 6 * 4;  // per lane and prefix-product slot
+constexpr int kWideSlotBytes = 5 * 4;  // per lane and prefix-product slot
 cudaError_t convert_coef_wide(const double *coef_dd, uint32_t *coef_wide, int64_t M, cudaStream_t s);
 cudaError_t launch_powers_wide(const PowerParams &p, cudaStream_t s);
 cudaError_t prepare_main_wide(size_t smem_bytes);

@@ -28,7 +28,7 @@ using wide::WF;
 using wide::WV;
 
 constexpr int kWideWords = 12;  // 32-bit words per stored full value (48 bytes)
-constexpr int kSlotWords = 6;   // words per lane in a prefix-product slot
+constexpr int kSlotWords = 5;   // words per lane in a prefix-product slot (4 limbs, sign | exponent)
 
 __global__ void convert_coef_kernel(const double *coef_dd, uint32_t *coef_wide, int64_t M) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -85,13 +85,13 @@ __device__ __forceinline__ void store_slot(uint32_t *slots, int j, int lane, con
   b[32] = v.m.w1;
   b[64] = v.m.w2;
   b[96] = v.m.w3;
-  b[128] = v.s;
-  b[160] = static_cast<uint32_t>(v.e);
+  b[128] = v.s | (static_cast<uint32_t>(v.e) & 0x7fffffffu);  // exponents fit in 31 bits
 }
 
 __device__ __forceinline__ WV load_slot(const uint32_t *slots, int j, int lane) {
   const uint32_t *b = slots + j * (kSlotWords * 32) + lane;
-  return WV{wide::Mag{b[0], b[32], b[64], b[96]}, b[128], static_cast<int32_t>(b[160])};
+  const uint32_t se = b[128];
+  return WV{wide::Mag{b[0], b[32], b[64], b[96]}, se & wide::kSignBit, static_cast<int32_t>(se << 1) >> 1};
 }
 
 __device__ __forceinline__ void accumulate_dd(double *p, int c, bool valid, dd x) {
@@ -137,10 +137,12 @@ __device__ void process_item_wide(const MainParams &kp, const Item &it, uint32_t
       const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
       if (a >= 2) G = wide::mul_x(G, wide::load_wf(tel(a - 1, v)), c);
     }
-    // Stage 2, forward: slot j <- G x_{i_1} ... x_{i_j}
+    // Stage 2, forward: P_j = G x_{i_1} ... x_{i_j}; every kp.slot_stride-th
+    // one is kept (slot j / stride), the others are recomputed below
+    const int stride = kp.slot_stride;
     WV Pc = G;
     for (int j = 0; j < k - 1; j++) {
-      store_slot(slots, j, lane, Pc);
+      if (j % stride == 0) store_slot(slots, j / stride, lane, Pc);
       const int v = static_cast<int>(__ldg(vw + j) & 0xffffu);
       Pc = wide::mul_x(Pc, wide::load_wf(tel(1, v)), c);
     }
@@ -154,7 +156,10 @@ __device__ void process_item_wide(const MainParams &kp, const Item &it, uint32_t
     for (int j = k - 2; j >= 0; j--) {
       const uint32_t w = __ldg(vw + j);
       const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
-      const WV D = wide::mul_pair(load_slot(slots, j, lane), Q, c);
+      WV Pj = load_slot(slots, j / stride, lane);
+      for (int r = j - j % stride; r < j; r++)  // recompute P_j from the kept P_{j - j % stride}
+        Pj = wide::mul_x(Pj, wide::load_wf(tel(1, static_cast<int>(__ldg(vw + r) & 0xffffu))), c);
+      const WV D = wide::mul_pair(Pj, Q, c);
       accumulate_dd(jel(v), c, valid, wide::to_dd(a == 1 ? D : wide::mul_small(D, static_cast<uint32_t>(a))));
       if (j > 0) Q = wide::mul_x(Q, wide::load_wf(tel(1, v)), c);
     }
