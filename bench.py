@@ -199,29 +199,32 @@ def run_reference(args, rank, world):
 
 
 class Workload:
-    """The batch one step evaluates, in double-double and in double, with its
-    device buffers and pinned host buffers."""
+    """The batch one step evaluates, with an evaluator per precision
+    ("dd": double-double on the FP64 pipe, "ddint": integer-pipe products,
+    "f64": complex double), device buffers and pinned host buffers."""
 
-    def __init__(self, cfg, rank, dev, primary):
+    def __init__(self, cfg, rank, dev):
         import torch
 
         import paper_1201_0499_gb300 as pkg
 
         self.pkg, self.torch, self.dev, self.cfg = pkg, torch, dev, cfg
-        prim = pkg.PE_DD_INT if primary == "ddint" else pkg.PE_DD
+        codes = {"dd": pkg.PE_DD, "ddint": pkg.PE_DD_INT, "f64": pkg.PE_F64}
         if cfg == 4:
             systems, pts = synth.config(4)
             self.text = synth.CONFIG_TEXT[4] + ", one launch"
-            self.many = {True: pkg.PolyEvalMany(systems, [p.shape[1] for p in pts], prim),
-                         False: pkg.PolyEvalMany([s.as_fp64() for s in systems], [p.shape[1] for p in pts],
-                                                 pkg.PE_F64)}
-            self.points = sum(p.shape[1] for p in pts)
+            npts = [p.shape[1] for p in pts]
+            self.ev = {k: pkg.PolyEvalMany(systems if k != "f64" else [s.as_fp64() for s in systems], npts, code)
+                       for k, code in codes.items()}
+            self.points = sum(npts)
             self.bufs = {}
-            for dd, ev in self.many.items():
+            for fmt in ("dd", "f64"):
+                ev = self.ev[fmt]
                 b = ev.buffers(dev)
-                ev.pack_points([torch.from_numpy(p if dd else np.ascontiguousarray(p[..., [0, 2]])) for p in pts], b[0])
-                self.bufs[dd] = b
-            self.host = [t.cpu().pin_memory() for t in self.bufs[True]]
+                ev.pack_points([torch.from_numpy(p if fmt == "dd" else np.ascontiguousarray(p[..., [0, 2]]))
+                                for p in pts], b[0])
+                self.bufs[fmt] = b
+            self.host = [t.cpu().pin_memory() for t in self.bufs["dd"]]
             self.system, self.pts = systems, pts
         else:
             if cfg == CONFIG_INDEX:
@@ -235,48 +238,48 @@ class Workload:
                 self.text = synth.CONFIG_TEXT[cfg]
             n, N = system.n_vars, system.n_polys
             self.system, self.pts, self.points = system, pts, P
-            self.single = {True: pkg.PolyEval(system, prim, max_points=P),
-                           False: pkg.PolyEval(system.as_fp64(), pkg.PE_F64, max_points=P)}
+            self.ev = {k: pkg.PolyEval(system if k != "f64" else system.as_fp64(), code, max_points=P)
+                       for k, code in codes.items()}
             self.bufs = {}
-            for dd in (True, False):
-                c = 4 if dd else 2
-                x = torch.from_numpy(pts if dd else np.ascontiguousarray(pts[..., [0, 2]])).to(dev)
-                self.bufs[dd] = (x, torch.empty((N, P, c), dtype=torch.float64, device=dev),
-                                 torch.empty((N, n, P, c), dtype=torch.float64, device=dev))
+            for fmt in ("dd", "f64"):
+                c = 4 if fmt == "dd" else 2
+                x = torch.from_numpy(pts if fmt == "dd" else np.ascontiguousarray(pts[..., [0, 2]])).to(dev)
+                self.bufs[fmt] = (x, torch.empty((N, P, c), dtype=torch.float64, device=dev),
+                                  torch.empty((N, n, P, c), dtype=torch.float64, device=dev))
             self.host = [torch.from_numpy(pts).pin_memory(), torch.empty((N, P, 4), dtype=torch.float64).pin_memory(),
                          torch.empty((N, n, P, 4), dtype=torch.float64).pin_memory()]
         self.h2d_bytes = int(self.host[0].numel() * 8)
         self.d2h_bytes = int((self.host[1].numel() + self.host[2].numel()) * 8)
 
-    def handle(self, dd):
-        return self.many[dd].handle if self.cfg == 4 else self.single[dd].handle
+    def handle(self, prec):
+        return self.ev[prec].handle
 
-    def eval(self, dd):
-        x, f, J = self.bufs[dd]
+    def eval(self, prec):
+        x, f, J = self.bufs["f64" if prec == "f64" else "dd"]
         if self.cfg == 4:
-            self.many[dd].eval_buffers(x, f, J)
+            self.ev[prec].eval_buffers(x, f, J)
         else:
-            self.single[dd].eval(x, f, J)
+            self.ev[prec].eval(x, f, J)
 
-    def eval_host(self):
+    def eval_host(self, prec):
         """Host points in, host f and J out, through the public entry points."""
         if self.cfg == 4:
-            x, f, J = self.bufs[True]
+            x, f, J = self.bufs["dd"]
             x.copy_(self.host[0], non_blocking=True)
-            self.many[True].eval_buffers(x, f, J)
+            self.ev[prec].eval_buffers(x, f, J)
             self.host[1].copy_(f, non_blocking=True)
             self.host[2].copy_(J, non_blocking=True)
             self.torch.cuda.current_stream().synchronize()
         else:
             hp, hf, hJ = self.host
-            self.pkg.polyeval_eval_host(self.single[True].handle, hp, self.points, hf, hJ,
+            self.pkg.polyeval_eval_host(self.ev[prec].handle, hp, self.points, hf, hJ,
                                         self.torch.cuda.current_stream())
 
-    def cost_per_launch(self):
+    def cost_per_launch(self, prec):
         """FP64 instructions and flops of one main-kernel launch."""
         if self.cfg == 4:
-            return self.many[True].cost()  # a batch handle reports whole-evaluation totals
-        ops, flops = self.single[True].cost()
+            return self.ev[prec].cost()  # a batch handle reports whole-evaluation totals
+        ops, flops = self.ev[prec].cost()
         return ops * self.points, flops * self.points
 
 
@@ -312,48 +315,50 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    wl = Workload(args.config, rank, dev, args.precision)
+    wl = Workload(args.config, rank, dev)
+    prim = args.precision
+    other = "ddint" if prim == "dd" else "dd"
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def timed_loop(dd, steps):
+    def timed_loop(prec, steps):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         for i in range(steps):
             flush.zero_()  # L2 flush between timed steps (outside the step's events)
             starts[i].record(stream)
-            wl.eval(dd)
+            wl.eval(prec)
             stops[i].record(stream)
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in zip(starts, stops))
 
     for _ in range(args.warmup):
-        wl.eval(True)
+        wl.eval(prim)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    pkg.polyeval_timing(wl.handle(True), True)
+    pkg.polyeval_timing(wl.handle(prim), True)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.time()
-    total_ms = timed_loop(True, args.steps)
+    total_ms = timed_loop(prim, args.steps)
     t_wall1 = time.time()
     if dist is not None:
         dist.barrier()
-    kern_ms, launches, kernels = pkg.polyeval_timing_read(wl.handle(True))
-    pkg.polyeval_timing(wl.handle(True), False)
+    kern_ms, launches, kernels = pkg.polyeval_timing_read(wl.handle(prim))
+    pkg.polyeval_timing(wl.handle(prim), False)
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
-    assert pkg.polyeval_status(wl.handle(True)) == pkg.PE_OK
+    assert pkg.polyeval_status(wl.handle(prim)) == pkg.PE_OK
 
     P = wl.points
     ms_per_step = max_over_ranks(total_ms / args.steps, dist)
     value = job_throughput(world, P, ms_per_step)
 
     # roofline of the main (monomial) kernel: FP64 pipe bound
-    ops_launch, flops_launch = wl.cost_per_launch()
+    ops_launch, flops_launch = wl.cost_per_launch(prim)
     kern_avg_ms = kern_ms / max(launches, 1)
     achieved_tflops = flops_launch / (kern_avg_ms * 1e-3) / 1e12
     peaks = peaks_file()
@@ -363,20 +368,23 @@ def main():
     peak_probe = 2 * fma_rate / 1e12
     issue_rate = ops_launch / (kern_avg_ms * 1e-3)
 
-    # complex double path on the same workload, same harness
-    for _ in range(args.warmup):
-        wl.eval(False)
-    k64 = max(args.steps, 10) if args.config == CONFIG_INDEX else args.steps
-    ms64 = timed_loop(False, k64) / k64
+    # complex double path and the other double-double path on the same workload, same harness
+    legs = {}
+    for leg in ("f64", other):
+        for _ in range(args.warmup):
+            wl.eval(leg)
+        kl = max(args.steps, 10) if args.config == CONFIG_INDEX else args.steps
+        legs[leg] = max_over_ranks(timed_loop(leg, kl) / kl, dist)
+    ms64 = legs["f64"]
 
     # end to end through the public API: pinned host in, pinned host out
     for _ in range(max(args.warmup, 1)):
-        wl.eval_host()
+        wl.eval_host(prim)
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        wl.eval_host()
+        wl.eval_host(prim)
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist)
 
     cpu = None
@@ -417,7 +425,12 @@ def main():
                          "probe_sm_mhz": probe_mhz,
                          "fp64_issue_frac": issue_rate / (SMS * DFMA_PER_SM_CLK * sm_max * 1e6)},
             "fp64_path": {"evals_per_s": job_throughput(world, P, ms64), "ms_per_step": ms64},
-            "dd_fp64_time_ratio": ms_per_step / ms64,
+            "dd_fp64_time_ratio": (ms_per_step if prim == "dd" else legs["dd"]) / ms64,
+            ("int_pipe_path" if other == "ddint" else "fp64_dd_path"): {
+                "evals_per_s": job_throughput(world, P, legs[other]), "ms_per_step": legs[other],
+                "speedup_vs_fp64_dd": (ms_per_step / legs[other]) if other == "ddint" else (legs[other] / ms_per_step),
+                "precision": ("complex double-double in/out, products in 128-bit integer block floating point, "
+                              "sums in double-double" if other == "ddint" else "complex double-double on the FP64 pipe")},
             "fp64_peak_frac": achieved_tflops / peak_nominal,
             "clocks": clocks,
         }
