@@ -164,6 +164,28 @@ PE_API int polyeval_create(const pe_system *sys, int precision, uint32_t flags, 
 PE_API int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream);
 
 /*
+ * One Newton step x <- x + dx, J(x) dx = -f(x), at P points of a square
+ * system (n_polys == n_vars).  Evaluating f and J is the expensive part of
+ * Newton's method, the corrector of a path tracker (Section 1); this entry
+ * point adds the linear solve so that a caller can correct a batch of
+ * points in one call.
+ *   points  device [n][P], updated in place (points whose Jacobian has an
+ *           exact zero pivot column are left unchanged)
+ *   out_f   device [n][P]: on return dx (not f)
+ *   out_J   device [n][n][P]: on return the LU factors (unit lower triangle
+ *           below the diagonal, after the row exchanges of partial pivoting)
+ *   norms   device [P][2] doubles or NULL: max_i |f_i(x)| before the step and
+ *           max_i |dx_i| (NaN for a singular point)
+ *   stream  as polyeval_eval
+ * The solve is LU with partial pivoting per point (pivot of largest modulus)
+ * in the handle's precision (double-double for PE_DD and PE_DD_INT, double
+ * for PE_F64), one lane pair per point.  Allocates nothing.  Errors: those of
+ * polyeval_eval; PE_EINVAL for a batch handle or a non-square system.
+ */
+PE_API int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, void *out_J, double *norms,
+                           void *stream);
+
+/*
  * polyeval_eval with HOST buffers: copies points to the device, evaluates,
  * and copies f and J back, all on `stream`, then synchronises the stream.
  * Host buffers should be pinned for full copy speed.  Device staging

@@ -34,6 +34,7 @@ from ._binding import (  # noqa: F401
     polyeval_eval_many,
     polyeval_eval_noalloc,
     polyeval_fp64_peak,
+    polyeval_newton,
     polyeval_many_layout,
     polyeval_status,
     polyeval_strerror,

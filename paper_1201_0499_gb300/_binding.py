@@ -86,6 +86,7 @@ def load_library(path: Optional[str] = None):
         "polyeval_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "polyeval_fp64_peak": ([P, D, D], ctypes.c_int),
         "polyeval_eval_noalloc": ([ctypes.POINTER(pe_system), I32, I32, P, I64, P, P, P], ctypes.c_int),
+        "polyeval_newton": ([P, P, I64, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -179,6 +180,12 @@ def polyeval_create_many(systems: Sequence, points_per_system: Sequence[int], pr
 def polyeval_eval(h: int, points, P: int, out_f, out_J, stream=None) -> None:
     _check(load_library().polyeval_eval(h, _addr(points), int(P), _addr(out_f), _addr(out_J), _stream(stream)),
            "polyeval_eval")
+
+
+def polyeval_newton(h: int, points, P: int, out_f, out_J, norms=None, stream=None) -> None:
+    """One Newton step at P points (points updated in place; out_f receives dx)."""
+    _check(load_library().polyeval_newton(h, _addr(points), int(P), _addr(out_f), _addr(out_J), _addr(norms),
+                                          _stream(stream)), "polyeval_newton")
 
 
 def polyeval_eval_host(h: int, points, P: int, out_f, out_J, stream=None) -> None:
@@ -275,6 +282,22 @@ class PolyEval:
             out_J = torch.empty((self.n_polys, self.n_vars, P, c), dtype=torch.float64, device=points.device)
         polyeval_eval(self.handle, points, P, out_f, out_J, stream)
         return out_f, out_J
+
+    def newton(self, points, out_dx=None, out_J=None, norms=None, stream=None):
+        """One Newton step; ``points`` (CUDA tensor [n, P, c]) is updated in
+        place.  Returns (dx, LU, norms [P, 2])."""
+        import torch
+
+        c = _elem(self.precision)
+        P = points.shape[1]
+        if out_dx is None:
+            out_dx = torch.empty((self.n_polys, P, c), dtype=torch.float64, device=points.device)
+        if out_J is None:
+            out_J = torch.empty((self.n_polys, self.n_vars, P, c), dtype=torch.float64, device=points.device)
+        if norms is None:
+            norms = torch.empty((P, 2), dtype=torch.float64, device=points.device)
+        polyeval_newton(self.handle, points, P, out_dx, out_J, norms, stream)
+        return out_dx, out_J, norms
 
     def cost(self):
         return polyeval_cost(self.handle)

@@ -120,6 +120,28 @@ __device__ __forceinline__ dd scale(dd x, double k) {
   return dd{p, __fma_rn(x.l, k, e)};
 }
 
+// Product of two double-doubles, renormalised (7 FP64 instructions).
+__device__ __forceinline__ dd mul(dd a, dd b) {
+  const double p = __dmul_rn(a.h, b.h);
+  double t = __fma_rn(a.h, b.h, -p);
+  t = __fma_rn(a.h, b.l, t);
+  t = __fma_rn(a.l, b.h, t);
+  return normalize(dd{p, t});
+}
+
+// 1 / d for a double-double d: the double reciprocal q of d.h refined by one
+// Newton step, q + q (1 - d q), with the residual 1 - d q formed from an
+// exact product (error about 2 u^2 relative).
+__device__ __forceinline__ dd recip(dd d) {
+  const double q = __ddiv_rn(1.0, d.h);
+  const double p = __dmul_rn(d.h, q);
+  const double pe = __fma_rn(d.h, q, -p);  // d.h q = p + pe exactly
+  double e = __dsub_rn(1.0, p);            // exact: p is within an ulp of 1
+  e = __dsub_rn(e, pe);
+  e = __fma_rn(-d.l, q, e);
+  return normalize(dd{q, __dmul_rn(q, e)});
+}
+
 __device__ __forceinline__ dd negate_if(dd x, unsigned long long sign_mask) {
   return dd{__longlong_as_double(__double_as_longlong(x.h) ^ static_cast<long long>(sign_mask)),
             __longlong_as_double(__double_as_longlong(x.l) ^ static_cast<long long>(sign_mask))};

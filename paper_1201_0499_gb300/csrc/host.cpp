@@ -587,6 +587,24 @@ int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, voi
   return PE_OK;
 }
 
+int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, void *out_J, double *norms, void *stream) {
+  if (!h || h->batch) return PE_EINVAL;
+  const SysDesc &d = h->sys[0];
+  if (d.N != d.n) return PE_EINVAL;
+  int rc = polyeval_eval(h, points, P, out_f, out_J, stream);
+  if (rc != PE_OK || P == 0) return rc;
+  pe::NewtonParams np{};
+  np.n = d.n;
+  np.P = P;
+  np.J = static_cast<double *>(out_J);
+  np.f = static_cast<double *>(out_f);
+  np.x = static_cast<double *>(points);
+  np.norms = norms;
+  if (pe::launch_newton(h->dd, np, static_cast<cudaStream_t>(stream)) != cudaSuccess) return PE_ECUDA;
+  h->kernels_launched++;
+  return PE_OK;
+}
+
 int polyeval_eval_many(polyeval_t *h, const void *points, void *out_f, void *out_J, void *stream) {
   if (!h || !h->batch) return PE_EINVAL;
   if (h->n_items_batch == 0) return PE_OK;

@@ -82,6 +82,17 @@ cudaError_t fp64_peak_probe(cudaStream_t s, double *fma_per_s, double *sm_clock_
 cudaError_t launch_combine(bool dd, double *out_f, double *out_J, const double *scratch_f, const double *scratch_J,
                            int64_t f_doubles, int64_t J_doubles, int chunks, cudaStream_t s);
 
+// Newton step (newton.cu): solve J dx = -f per point, x += dx.
+struct NewtonParams {
+  int32_t n;        // variables = polynomials
+  int64_t P;        // points
+  double *J;        // [n][n][P] Jacobian, factored in place
+  double *f;        // [n][P] f on entry, dx on return
+  double *x;        // [n][P] points, updated in place
+  double *norms;    // [P][2] (|f|_inf, |dx|_inf) or nullptr
+};
+cudaError_t launch_newton(bool dd, const NewtonParams &p, cudaStream_t s);
+
 // Integer-pipe evaluation (kernels_wide.cu): 128-bit block floating point
 // products, double-double sums.  Table entries and coefficients are 48 bytes.
 constexpr int kWideBytes = 48;

@@ -371,3 +371,74 @@ def test_config5_large_sampled(prec):
         Sf, SJ = scales(s, pts[:, sub])
         assert normwise_vs(f[:, sub], Fo, Sf) <= DD_TOL
         assert normwise_vs(J[:, :, sub], Jo, SJ) <= DD_TOL
+
+
+# ----------------------------------------------------------------------------
+# bounds and chunking
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_outputs_do_not_touch_guard_bands(prec):
+    """f and J written through views inside larger buffers filled with a
+    canary: nothing outside the views changes (no out-of-bounds stores,
+    including the lanes past a ragged tail and the chunk scratch)."""
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+    from _util import pe_precision
+
+    s = random_system(121, n=9, N=7, m=6, kmin=0, kmax=4, emax=4)
+    for P in (1, 5, 17, 40):
+        pts = synth.points(122 + P, 9, P)
+        dd = prec != "f64"
+        c = 4 if dd else 2
+        x = to_device(pts, dd)
+        guard = 1000
+        canary = -1.2345e300
+        fbuf = torch.full((7 * P * c + 2 * guard,), canary, dtype=torch.float64, device="cuda")
+        Jbuf = torch.full((7 * 9 * P * c + 2 * guard,), canary, dtype=torch.float64, device="cuda")
+        f = fbuf[guard:guard + 7 * P * c].view(7, P, c)
+        J = Jbuf[guard:guard + 7 * 9 * P * c].view(7, 9, P, c)
+        ev = pkg.PolyEval(s if dd else s.as_fp64(), pe_precision(prec), max_points=P)
+        ev.eval(x, f, J)
+        torch.cuda.synchronize()
+        assert ev.status() == pkg.PE_OK
+        for buf in (fbuf, Jbuf):
+            assert torch.all(buf[:guard] == canary) and torch.all(buf[-guard:] == canary)
+        assert not torch.any(f == canary) and not torch.any(J == canary)
+        fo, Jo = f.cpu().numpy(), J.cpu().numpy()
+        if not dd:
+            from _util import widen
+
+            fo, Jo = widen(fo), widen(Jo)
+        check_exact_oracle(s, pts, fo, Jo, tol(prec), dd=dd)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_more_chunks_than_monomials(prec):
+    """One point and polynomials of 1..3 monomials: the call splits the
+    monomials into up to 8 chunks, most of them empty."""
+    s = random_system(123, n=4, N=3, m=2, kmin=1, kmax=3, emax=3)
+    pts = synth.points(124, 4, 1)
+    f, J = run(s, pts, prec)
+    check_exact_oracle(s, pts, f, J, tol(prec), dd=prec != "f64")
+
+
+def test_integer_path_deterministic_and_close_to_fp64_dd():
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+
+    s, pts = synth.config(2, n_points=200)
+    x = to_device(pts)
+    a = pkg.PolyEval(s, pkg.PE_DD_INT, max_points=200)
+    f1, J1 = a.eval(x)
+    f2, J2 = a.eval(x)
+    torch.cuda.synchronize()
+    assert torch.equal(f1, f2) and torch.equal(J1, J2)
+    b = pkg.PolyEval(s, pkg.PE_DD, max_points=200)
+    f3, J3 = b.eval(x)
+    torch.cuda.synchronize()
+    Sf, SJ = scales(s, pts)
+    assert normwise_vs(f1.cpu().numpy(), f3.cpu().numpy(), Sf) <= 2 * DD_TOL
+    assert normwise_vs(J1.cpu().numpy(), J3.cpu().numpy(), SJ) <= 2 * DD_TOL

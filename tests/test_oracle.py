@@ -425,3 +425,60 @@ def test_c_dd_oracle_point_range_and_args():
     assert np.any(F[:, 1] != 0)
     with pytest.raises(ValueError):
         oracle.dd_eval(s, pts, q0=3, q1=2)
+
+
+# ----------------------------------------------------------------------------
+# the exact Newton step
+# ----------------------------------------------------------------------------
+
+def test_newton_exact_on_linear_system_lands_on_solution():
+    """f = A x - b: one Newton step from any x0 gives A x1 = b (checked by a
+    plain matrix-vector product)."""
+    from oracle import newton as N
+
+    rng = np.random.Generator(np.random.PCG64(31))
+    n = 4
+    A = rng.integers(-3, 4, size=(n, n)) + 1j * rng.integers(-3, 4, size=(n, n)) + 5 * np.eye(n)
+    b = rng.integers(-3, 4, size=n) + 1j * rng.integers(-3, 4, size=n)
+    polys, coef = [], []
+    for p in range(n):
+        mons = [([i], [1]) for i in range(n) if A[p, i] != 0] + [([], [])]
+        coef += [[A[p, i].real, 0, A[p, i].imag, 0] for i in range(n) if A[p, i] != 0]
+        coef.append([-b[p].real, 0, -b[p].imag, 0])
+        polys.append(mons)
+    s = synth.from_monomials(n, polys, coef)
+    pts = synth.points(32, n, 1)
+    _f, _J, _dx, x1 = N.newton_step(s, pts, 0)
+    for p in range(n):
+        acc = N.ZERO
+        for i in range(n):
+            acc = N.c_add(acc, N.c_mul((Fraction(A[p, i].real), Fraction(A[p, i].imag)), x1[i]))
+        assert acc == (Fraction(b[p].real), Fraction(b[p].imag))
+
+
+def test_newton_exact_univariate_closed_form():
+    """f = x^2 - c: x1 = (x0^2 + c) / (2 x0)."""
+    from oracle import newton as N
+
+    c = complex(2, 1)
+    s = synth.from_monomials(1, [[([0], [2]), ([], [])]], [[1, 0, 0, 0], [-c.real, 0, -c.imag, 0]])
+    pts = np.array([[[1.5, 0, 0.25, 0]]])
+    _f, _J, _dx, x1 = N.newton_step(s, pts, 0)
+    x0 = (Fraction(1.5), Fraction(0.25))
+    want = N.c_div(N.c_add(N.c_mul(x0, x0), (Fraction(2), Fraction(1))), N.c_mul((Fraction(2), Fraction(0)), x0))
+    assert x1[0] == want
+
+
+def test_newton_exact_residual_identity():
+    """J dx = -f exactly for a random square system."""
+    from oracle import newton as N
+
+    s = random_dd_system(33, n=3, N=3, m=4, kmax=3, emax=3, allow_k0=True)
+    pts = synth.points(34, 3, 2)
+    for q in range(2):
+        f, J, dx, _ = N.newton_step(s, pts, q)
+        for i in range(3):
+            acc = f[i]
+            for j in range(3):
+                acc = N.c_add(acc, N.c_mul(J[i][j], dx[j]))
+            assert acc == N.ZERO
