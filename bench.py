@@ -293,6 +293,8 @@ def main():
     ap.add_argument("--precision", default="dd", choices=["dd", "ddint"],
                     help="dd: double-double on the FP64 pipe; ddint: products in 128-bit integer block "
                          "floating point, sums in double-double (same inputs, outputs and accuracy bar)")
+    ap.add_argument("--graph", action="store_true",
+                    help="replay the evaluation from a captured CUDA graph in the timed steps")
     ap.add_argument("--config", type=int, default=CONFIG_INDEX, choices=[2, 3, 4, 5],
                     help="workload (default 2, the benchmark workload; 3, 4, 5: the larger and ragged ones)")
     args = ap.parse_args()
@@ -320,19 +322,39 @@ def main():
     other = "ddint" if prim == "dd" else "dd"
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    graphs = {}
+
+    def step(prec):
+        if prec in graphs:
+            graphs[prec].replay()
+        else:
+            wl.eval(prec)
+
     def timed_loop(prec, steps):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         for i in range(steps):
             flush.zero_()  # L2 flush between timed steps (outside the step's events)
             starts[i].record(stream)
-            wl.eval(prec)
+            step(prec)
             stops[i].record(stream)
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in zip(starts, stops))
 
+    if args.graph:
+        # capture one evaluation per precision; the library call queues only
+        # kernels and a memset on the capturing stream
+        for prec in ("dd", "ddint", "f64"):
+            wl.eval(prec)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                wl.eval(prec)
+            graphs[prec] = g
+        torch.cuda.synchronize()
+
     for _ in range(args.warmup):
-        wl.eval(prim)
+        step(prim)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
@@ -350,6 +372,17 @@ def main():
     kern_ms, launches, kernels = pkg.polyeval_timing_read(wl.handle(prim))
     pkg.polyeval_timing(wl.handle(prim), False)
     sampler.stop()
+    if graphs:
+        # graph replays record no library events: time the main kernel on an
+        # eager pass of the same evaluation, and count the graph's kernels
+        pkg.polyeval_timing(wl.handle(prim), True)
+        kt = min(args.steps, 20)
+        for _ in range(kt):
+            flush.zero_()
+            wl.eval(prim)
+        kern_ms, launches, k_eager = pkg.polyeval_timing_read(wl.handle(prim))
+        pkg.polyeval_timing(wl.handle(prim), False)
+        kernels = (k_eager // max(kt, 1)) * args.steps
     clocks = sampler.summary(t_wall0, t_wall1)
     assert pkg.polyeval_status(wl.handle(prim)) == pkg.PE_OK
 
@@ -372,10 +405,37 @@ def main():
     legs = {}
     for leg in ("f64", other):
         for _ in range(args.warmup):
-            wl.eval(leg)
+            step(leg)
         kl = max(args.steps, 10) if args.config == CONFIG_INDEX else args.steps
         legs[leg] = max_over_ranks(timed_loop(leg, kl) / kl, dist)
     ms64 = legs["f64"]
+
+    # Newton step (evaluation + LU solve per point + update) with the primary precision
+    newton = None
+    if args.config != 4:
+        ev_p = wl.ev[prim]
+        x0 = wl.bufs["dd"][0].clone()
+        xn = x0.clone()
+        dx = torch.empty_like(wl.bufs["dd"][1])
+        lu = torch.empty_like(wl.bufs["dd"][2])
+        nrm = torch.empty((P, 2), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            xn.copy_(x0)
+            pkg.polyeval_newton(ev_p.handle, xn, P, dx, lu, nrm, stream)
+        kn = max(min(args.steps, 50), 3)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(kn)]
+        stops = [torch.cuda.Event(enable_timing=True) for _ in range(kn)]
+        for i in range(kn):
+            xn.copy_(x0)
+            flush.zero_()
+            starts[i].record(stream)
+            pkg.polyeval_newton(ev_p.handle, xn, P, dx, lu, nrm, stream)
+            stops[i].record(stream)
+        torch.cuda.synchronize()
+        ms_newton = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, stops)) / kn, dist)
+        newton = {"ms_per_step": ms_newton, "solve_ms": ms_newton - ms_per_step,
+                  "points_per_s": job_throughput(world, P, ms_newton),
+                  "what": "f, J, LU with partial pivoting per point, x += dx (polyeval_newton)"}
 
     # end to end through the public API: pinned host in, pinned host out
     for _ in range(max(args.warmup, 1)):
@@ -410,6 +470,7 @@ def main():
                        "precision": ("complex double-double" if args.precision == "dd" else
                                      "complex double-double in/out, products in 128-bit integer block floating point"),
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                       "cuda_graph": bool(args.graph),
                        "launch": f"{kernels // max(args.steps, 1)} kernels per step (power table, monomial "
                                  "kernel, combine of monomial chunks when the call has few items)"},
             "e2e": {"value": job_throughput(world, P, e2e_ms), "unit": "evals/s",
@@ -432,6 +493,7 @@ def main():
                 "precision": ("complex double-double in/out, products in 128-bit integer block floating point, "
                               "sums in double-double" if other == "ddint" else "complex double-double on the FP64 pipe")},
             "fp64_peak_frac": achieved_tflops / peak_nominal,
+            "newton_step": newton,
             "clocks": clocks,
         }
         if cpu is not None:

@@ -3,123 +3,212 @@
 // solve J(x) dx = -f(x) by LU decomposition with partial pivoting, then
 // x <- x + dx.
 //
-// One lane pair per point (lanes 2q and 2q+1: real and imaginary parts), in
-// the precision of the evaluation (double-double, or double).  The Jacobian
-// the evaluator wrote ([N][n][P], point index fastest) is factored in place:
-// every load and store of a warp covers 16 consecutive points, coalesced.
-// Right-hand side and solution overwrite f.
+// One warp per point.  The Jacobian the evaluator wrote ([N][n][P], point
+// index fastest) is factored in place; in elimination step k the lanes take
+// the columns j > k of the trailing rows (lane j, j + 32, ...), the pivot is
+// found by a warp-wide arg-max, the multipliers are formed by the lanes that
+// own their rows, and the back substitution reduces each row's dot product
+// across the warp.  Arithmetic in the precision of the evaluation
+// (complex double-double, or complex double).  Right-hand side and solution
+// overwrite f.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
 
-#include "arith.cuh"
+#include "dd.cuh"
 #include "internal.h"
 
 namespace pe {
 
-template <class A>
-__global__ void newton_solve(const NewtonParams p) {
-  using V = typename A::V;
-  constexpr int KD = A::kDoubles;
+namespace {
+
+constexpr unsigned kAll = 0xffffffffu;
+
+// complex double-double, both parts in one thread
+struct CDD {
+  static constexpr int kDoubles = 4;
+  dd re, im;
+  __device__ static CDD load(const double *p) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    const double2 b = reinterpret_cast<const double2 *>(p)[1];
+    return CDD{dd{a.x, a.y}, dd{b.x, b.y}};
+  }
+  __device__ void store(double *p) const {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(re.h, re.l);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(im.h, im.l);
+  }
+  __device__ static CDD zero() { return CDD{dd{0.0, 0.0}, dd{0.0, 0.0}}; }
+  __device__ double abs_hi() const { return sqrt(re.h * re.h + im.h * im.h); }
+  __device__ CDD neg() const { return CDD{negate_if(re, 0x8000000000000000ULL), negate_if(im, 0x8000000000000000ULL)}; }
+  // x * y, renormalised
+  __device__ static CDD mul(const CDD &x, const CDD &y) {
+    return CDD{dot2n(x.re, y.re, negate_if(x.im, 0x8000000000000000ULL), y.im), dot2n(x.re, y.im, x.im, y.re)};
+  }
+  // a - x * y, renormalised
+  __device__ static CDD sub_mul(const CDD &a, const CDD &x, const CDD &y) {
+    const dd pr = dot2(x.re, y.re, negate_if(x.im, 0x8000000000000000ULL), y.im);
+    const dd pi = dot2(x.re, y.im, x.im, y.re);
+    return CDD{normalize(add(a.re, negate_if(pr, 0x8000000000000000ULL))),
+               normalize(add(a.im, negate_if(pi, 0x8000000000000000ULL)))};
+  }
+  __device__ static CDD add2(const CDD &a, const CDD &b) { return CDD{add(a.re, b.re), add(a.im, b.im)}; }
+  __device__ CDD finish() const { return CDD{normalize(re), normalize(im)}; }
+  // 1 / z = conj(z) / |z|^2
+  __device__ static CDD recip(const CDD &z) {
+    const dd n2 = dot2n(z.re, z.re, z.im, z.im);
+    const dd r = pe::recip(n2);
+    return CDD{pe::mul(z.re, r), pe::mul(negate_if(z.im, 0x8000000000000000ULL), r)};
+  }
+  __device__ CDD shfl_down(int d) const {
+    return CDD{dd{__shfl_down_sync(kAll, re.h, d), __shfl_down_sync(kAll, re.l, d)},
+               dd{__shfl_down_sync(kAll, im.h, d), __shfl_down_sync(kAll, im.l, d)}};
+  }
+};
+
+// complex double
+struct C64 {
+  static constexpr int kDoubles = 2;
+  double re, im;
+  __device__ static C64 load(const double *p) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    return C64{a.x, a.y};
+  }
+  __device__ void store(double *p) const { reinterpret_cast<double2 *>(p)[0] = make_double2(re, im); }
+  __device__ static C64 zero() { return C64{0.0, 0.0}; }
+  __device__ double abs_hi() const { return sqrt(re * re + im * im); }
+  __device__ C64 neg() const { return C64{-re, -im}; }
+  __device__ static C64 mul(const C64 &x, const C64 &y) {
+    return C64{__fma_rn(x.re, y.re, -__dmul_rn(x.im, y.im)), __fma_rn(x.re, y.im, __dmul_rn(x.im, y.re))};
+  }
+  __device__ static C64 sub_mul(const C64 &a, const C64 &x, const C64 &y) {
+    const C64 p = mul(x, y);
+    return C64{__dsub_rn(a.re, p.re), __dsub_rn(a.im, p.im)};
+  }
+  __device__ static C64 add2(const C64 &a, const C64 &b) { return C64{__dadd_rn(a.re, b.re), __dadd_rn(a.im, b.im)}; }
+  __device__ C64 finish() const { return *this; }
+  __device__ static C64 recip(const C64 &z) {
+    const double r = __ddiv_rn(1.0, __fma_rn(z.re, z.re, __dmul_rn(z.im, z.im)));
+    return C64{__dmul_rn(z.re, r), -__dmul_rn(z.im, r)};
+  }
+  __device__ C64 shfl_down(int d) const {
+    return C64{__shfl_down_sync(kAll, re, d), __shfl_down_sync(kAll, im, d)};
+  }
+};
+
+}  // namespace
+
+template <class C>
+__global__ void newton_lu(const NewtonParams p) {
+  constexpr int KD = C::kDoubles;
   const int lane = threadIdx.x & 31;
-  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if (warp * kPointsPerWarp >= p.P) return;  // the whole warp is past the end
-  const int64_t q = warp * kPointsPerWarp + (lane >> 1);
-  const bool valid = q < p.P;
-  const int64_t qc = valid ? q : p.P - 1;  // lanes past the end compute on the last point and store nothing
-  const int c = lane & 1;
-  const unsigned long long sgn = c ? 0ULL : kSign;
-  const unsigned long long neg = kSign;
+  const int64_t q = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;  // one warp per point
+  if (q >= p.P) return;  // warp-uniform
   const int n = p.n;
   const size_t P = static_cast<size_t>(p.P);
-  auto Jel = [&](int i, int j) { return p.J + ((static_cast<size_t>(i) * n + j) * P + qc) * KD; };
-  auto Fel = [&](int i) { return p.f + (static_cast<size_t>(i) * P + qc) * KD; };
-  auto Xel = [&](int i) { return p.x + (static_cast<size_t>(i) * P + qc) * KD; };
-  auto mag = [&](V z) {  // |z| of the pair's complex value, from the high words
-    const double a = A::hi(z), b = A::hi(A::partner(z));
-    return sqrt(a * a + b * b);
-  };
+  auto Jel = [&](int i, int j) { return p.J + ((static_cast<size_t>(i) * n + j) * P + q) * KD; };
+  auto Fel = [&](int i) { return p.f + (static_cast<size_t>(i) * P + q) * KD; };
+  auto Xel = [&](int i) { return p.x + (static_cast<size_t>(i) * P + q) * KD; };
 
   // residual norm; right-hand side b = -f
   double fnorm = 0.0;
-  for (int i = 0; i < n; i++) {
-    const V fi = A::load_comp(Fel(i), c);
-    fnorm = fmax(fnorm, mag(fi));
-    if (valid) A::store_comp(Fel(i), c, A::neg_if(fi, neg));
+  for (int i = lane; i < n; i += 32) {
+    const C fi = C::load(Fel(i));
+    fnorm = fmax(fnorm, fi.abs_hi());
+    fi.neg().store(Fel(i));
   }
+  for (int d = 16; d > 0; d >>= 1) fnorm = fmax(fnorm, __shfl_xor_sync(kAll, fnorm, d));
+  __syncwarp();
 
   bool singular = false;
   for (int k = 0; k < n; k++) {
-    int piv = k;
+    // pivot: the row i >= k of largest |J[i][k]| (smallest index on ties)
     double best = -1.0;
-    for (int i = k; i < n; i++) {
-      const double m = mag(A::load_comp(Jel(i, k), c));
+    int piv = n;
+    for (int i = k + lane; i < n; i += 32) {
+      const double m = C::load(Jel(i, k)).abs_hi();
       if (m > best) {
         best = m;
         piv = i;
       }
     }
-    // a zero pivot column: this point's matrix is singular; the pair carries
-    // on with a zero multiplier (no branch around the shuffles below)
-    const bool zero_pivot = !(best > 0.0);
-    singular = singular || zero_pivot;
-    if (piv != k && valid) {
-      for (int j = k; j < n; j++) {
-        const V a = A::load_comp(Jel(k, j), c), b = A::load_comp(Jel(piv, j), c);
-        A::store_comp(Jel(k, j), c, b);
-        A::store_comp(Jel(piv, j), c, a);
+    for (int d = 16; d > 0; d >>= 1) {
+      const double ob = __shfl_xor_sync(kAll, best, d);
+      const int op = __shfl_xor_sync(kAll, piv, d);
+      if (ob > best || (ob == best && op < piv)) {
+        best = ob;
+        piv = op;
       }
-      const V a = A::load_comp(Fel(k), c), b = A::load_comp(Fel(piv), c);
-      A::store_comp(Fel(k), c, b);
-      A::store_comp(Fel(piv), c, a);
     }
-    V inv = recip_split<A>(A::load_comp(Jel(k, k), c), c);
-    if (zero_pivot) inv = A::zero();
-    const V bk = A::load_comp(Fel(k), c);
-    for (int i = k + 1; i < n; i++) {
-      const V l = mul_split<A, true>(A::load_comp(Jel(i, k), c), inv, c, sgn);  // multiplier l_ik
-      if (valid) A::store_comp(Jel(i, k), c, l);
-      for (int j = k + 1; j < n; j++) {
-        const V t = mul_split<A>(l, A::load_comp(Jel(k, j), c), c, sgn);
-        const V a = A::add(A::load_comp(Jel(i, j), c), A::neg_if(t, neg));
-        if (valid) A::store_comp(Jel(i, j), c, A::finish(a));
+    if (!(best > 0.0)) {  // warp-uniform: this point's matrix is singular
+      singular = true;
+      break;
+    }
+    if (piv != k) {
+      for (int j = k + lane; j < n; j += 32) {
+        const C a = C::load(Jel(k, j)), b = C::load(Jel(piv, j));
+        b.store(Jel(k, j));
+        a.store(Jel(piv, j));
       }
-      const V b = A::add(A::load_comp(Fel(i), c), A::neg_if(mul_split<A>(l, bk, c, sgn), neg));
-      if (valid) A::store_comp(Fel(i), c, A::finish(b));
+      if (lane == 0) {
+        const C a = C::load(Fel(k)), b = C::load(Fel(piv));
+        b.store(Fel(k));
+        a.store(Fel(piv));
+      }
+      __syncwarp();
     }
+    // multipliers l_i = J[i][k] / J[k][k] and the right-hand side, by the
+    // lanes that own rows i > k
+    const C inv = C::recip(C::load(Jel(k, k)));
+    const C bk = C::load(Fel(k));
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      const C l = C::mul(C::load(Jel(i, k)), inv);
+      l.store(Jel(i, k));
+      C::sub_mul(C::load(Fel(i)), l, bk).store(Fel(i));
+    }
+    __syncwarp();
+    // trailing update: lanes over the columns j > k
+    for (int j = k + 1 + lane; j < n; j += 32) {
+      const C u = C::load(Jel(k, j));
+      for (int i = k + 1; i < n; i++) C::sub_mul(C::load(Jel(i, j)), C::load(Jel(i, k)), u).store(Jel(i, j));
+    }
+    __syncwarp();
   }
 
-  // back substitution: dx overwrites the right-hand side
+  // back substitution, dx overwrites b; each row's dot product reduced across the warp
   double dxnorm = 0.0;
-  for (int i = n - 1; i >= 0; i--) {
-    V s = A::load_comp(Fel(i), c);
-    for (int j = i + 1; j < n; j++)
-      s = A::add(s, A::neg_if(mul_split<A>(A::load_comp(Jel(i, j), c), A::load_comp(Fel(j), c), c, sgn), neg));
-    V dx = mul_split<A, true>(A::finish(s), recip_split<A>(A::load_comp(Jel(i, i), c), c), c, sgn);
-    if (singular) dx = A::zero();
-    dxnorm = fmax(dxnorm, mag(dx));
-    if (valid) A::store_comp(Fel(i), c, dx);
-  }
-  // x <- x + dx
   if (!singular) {
-    for (int i = 0; i < n; i++) {
-      const V x = A::add(A::load_comp(Xel(i), c), A::load_comp(Fel(i), c));
-      if (valid) A::store_comp(Xel(i), c, A::finish(x));
+    for (int i = n - 1; i >= 0; i--) {
+      C s = C::zero();
+      for (int j = i + 1 + lane; j < n; j += 32) s = C::sub_mul(s, C::load(Jel(i, j)), C::load(Fel(j)));
+      for (int d = 16; d > 0; d >>= 1) s = C::add2(s, s.shfl_down(d));
+      if (lane == 0) {
+        const C xi = C::mul(C::add2(C::load(Fel(i)), s).finish(), C::recip(C::load(Jel(i, i))));
+        xi.store(Fel(i));
+        dxnorm = fmax(dxnorm, xi.abs_hi());
+      }
+      __syncwarp();
     }
+    dxnorm = __shfl_sync(kAll, dxnorm, 0);
+    // x <- x + dx
+    for (int i = lane; i < n; i += 32) C::add2(C::load(Xel(i)), C::load(Fel(i))).finish().store(Xel(i));
+  } else {
+    for (int i = lane; i < n; i += 32) C::zero().store(Fel(i));
   }
-  if (valid && p.norms) p.norms[q * 2 + c] = c == 0 ? fnorm : (singular ? nan("") : dxnorm);
+  if (lane == 0 && p.norms) {
+    p.norms[q * 2] = fnorm;
+    p.norms[q * 2 + 1] = singular ? nan("") : dxnorm;
+  }
 }
 
 cudaError_t launch_newton(bool dd, const NewtonParams &p, cudaStream_t s) {
   if (p.P <= 0 || p.n <= 0) return cudaSuccess;
-  const int64_t warps = (p.P + kPointsPerWarp - 1) / kPointsPerWarp;
-  const int threads = 64;
-  const int64_t blocks = (warps * 32 + threads - 1) / threads;
+  const int threads = 128;
+  const int64_t blocks = (p.P * 32 + threads - 1) / threads;
   if (dd)
-    newton_solve<ArithDD><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
+    newton_lu<CDD><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
   else
-    newton_solve<ArithF64><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
+    newton_lu<C64><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
