@@ -293,6 +293,8 @@ def main():
     ap.add_argument("--precision", default="dd", choices=["dd", "ddint"],
                     help="dd: double-double on the FP64 pipe; ddint: products in 128-bit integer block "
                          "floating point, sums in double-double (same inputs, outputs and accuracy bar)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip polyeval_autotune (launch choices from the built-in heuristic)")
     ap.add_argument("--graph", action="store_true",
                     help="replay the evaluation from a captured CUDA graph in the timed steps")
     ap.add_argument("--config", type=int, default=CONFIG_INDEX, choices=[2, 3, 4, 5],
@@ -321,6 +323,14 @@ def main():
     prim = args.precision
     other = "ddint" if prim == "dd" else "dd"
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    tuned = {}
+    if not args.no_autotune and args.config != 4:
+        # pick the launch per precision on this batch, before any timed step
+        for prec in ("dd", "ddint", "f64"):
+            x, f, J = wl.bufs["f64" if prec == "f64" else "dd"]
+            tuned[prec] = pkg.polyeval_autotune(wl.handle(prec), x, wl.points, f, J, stream)
+        torch.cuda.synchronize()
 
     graphs = {}
 
@@ -471,6 +481,8 @@ def main():
                                      "complex double-double in/out, products in 128-bit integer block floating point"),
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "cuda_graph": bool(args.graph),
+                       "autotuned_launch": {k: {"chunks": v[0], "shape": "one wave" if v[1] == 1 else "persistent"}
+                                            for k, v in tuned.items()},
                        "launch": f"{kernels // max(args.steps, 1)} kernels per step (power table, monomial "
                                  "kernel, combine of monomial chunks when the call has few items)"},
             "e2e": {"value": job_throughput(world, P, e2e_ms), "unit": "evals/s",

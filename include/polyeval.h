@@ -164,6 +164,21 @@ PE_API int polyeval_create(const pe_system *sys, int precision, uint32_t flags, 
 PE_API int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream);
 
 /*
+ * Choose the launch of polyeval_eval for P points by timing the candidates on
+ * the caller's data: the number of chunks the monomials of each polynomial
+ * are split into (1, 2, 4, 8, as the handle's scratch allows) and the launch
+ * shape (1: one single-warp block per work item, all resident at once; 2: a
+ * persistent grid taking items from the work counter).  Runs each candidate
+ * four times on `stream` (one warm-up, three timed with CUDA events),
+ * synchronises, keeps the fastest in the handle for later calls with the same
+ * P, and returns it in *chunks and *shape (either may be NULL).  The outputs
+ * hold a valid evaluation on return.  Not for use during stream capture.
+ * Errors: those of polyeval_eval.
+ */
+PE_API int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream,
+                             int *chunks, int *shape);
+
+/*
  * One Newton step x <- x + dx, J(x) dx = -f(x), at P points of a square
  * system (n_polys == n_vars).  Evaluating f and J is the expensive part of
  * Newton's method, the corrector of a path tracker (Section 1); this entry

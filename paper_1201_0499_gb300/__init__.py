@@ -25,6 +25,7 @@ from ._binding import (  # noqa: F401
     PolyEvalMany,
     load_library,
     pe_system,
+    polyeval_autotune,
     polyeval_cost,
     polyeval_create,
     polyeval_create_many,

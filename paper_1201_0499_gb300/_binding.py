@@ -87,6 +87,8 @@ def load_library(path: Optional[str] = None):
         "polyeval_fp64_peak": ([P, D, D], ctypes.c_int),
         "polyeval_eval_noalloc": ([ctypes.POINTER(pe_system), I32, I32, P, I64, P, P, P], ctypes.c_int),
         "polyeval_newton": ([P, P, I64, P, P, P, P], ctypes.c_int),
+        "polyeval_autotune": ([P, P, I64, P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                              ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -180,6 +182,15 @@ def polyeval_create_many(systems: Sequence, points_per_system: Sequence[int], pr
 def polyeval_eval(h: int, points, P: int, out_f, out_J, stream=None) -> None:
     _check(load_library().polyeval_eval(h, _addr(points), int(P), _addr(out_f), _addr(out_J), _stream(stream)),
            "polyeval_eval")
+
+
+def polyeval_autotune(h: int, points, P: int, out_f, out_J, stream=None):
+    """Time the launch candidates for P points and keep the fastest in the
+    handle; returns (chunks, shape)."""
+    c, m = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().polyeval_autotune(h, _addr(points), int(P), _addr(out_f), _addr(out_J), _stream(stream),
+                                            ctypes.byref(c), ctypes.byref(m)), "polyeval_autotune")
+    return c.value, m.value
 
 
 def polyeval_newton(h: int, points, P: int, out_f, out_J, norms=None, stream=None) -> None:
@@ -282,6 +293,18 @@ class PolyEval:
             out_J = torch.empty((self.n_polys, self.n_vars, P, c), dtype=torch.float64, device=points.device)
         polyeval_eval(self.handle, points, P, out_f, out_J, stream)
         return out_f, out_J
+
+    def autotune(self, points, out_f=None, out_J=None, stream=None):
+        """Tune the launch for this point count; returns (chunks, shape)."""
+        import torch
+
+        c = _elem(self.precision)
+        P = points.shape[1]
+        if out_f is None:
+            out_f = torch.empty((self.n_polys, P, c), dtype=torch.float64, device=points.device)
+        if out_J is None:
+            out_J = torch.empty((self.n_polys, self.n_vars, P, c), dtype=torch.float64, device=points.device)
+        return polyeval_autotune(self.handle, points.contiguous(), P, out_f, out_J, stream)
 
     def newton(self, points, out_dx=None, out_J=None, norms=None, stream=None):
         """One Newton step; ``points`` (CUDA tensor [n, P, c]) is updated in

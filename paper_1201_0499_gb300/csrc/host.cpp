@@ -81,6 +81,12 @@ struct polyeval {
   DeviceBuf poly_ptr, mono_ptr, var, coef, coef_wide, poly_sys, sysd, perm, items, prefix, table, counter, status;
   DeviceBuf stage_pts, stage_f, stage_J;
   DeviceBuf scratch;  // chunk partial results (single-system handles)
+  struct Tuned {
+    int64_t P;
+    int chunks;
+    int mode;  // 1: one single-warp block per item, 2: persistent grid
+  };
+  std::vector<Tuned> tuned;  // launch choices found by polyeval_autotune, per point count
   // timing of the main kernel
   bool timing = false;
   cudaEvent_t ev[2 * kMaxTimingEvents] = {};
@@ -300,8 +306,8 @@ struct Shape {
   size_t smem;
 };
 
-Shape shape_for(const polyeval *h, int64_t n_items) {
-  if (n_items <= static_cast<int64_t>(h->sms) * h->blocks_per_sm_1)
+Shape shape_for(const polyeval *h, int64_t n_items, int mode = 0) {
+  if (mode == 1 || (mode == 0 && n_items <= static_cast<int64_t>(h->sms) * h->blocks_per_sm_1))
     return Shape{static_cast<int>(std::max<int64_t>(1, n_items)), 1, h->smem_per_warp};
   const int64_t full = static_cast<int64_t>(h->sms) * h->blocks_per_sm;
   const int64_t need = (n_items + h->warps_per_block - 1) / h->warps_per_block;
@@ -327,7 +333,7 @@ pe::MainParams main_params(const polyeval *h) {
   return p;
 }
 
-int run_main(polyeval *h, const pe::MainParams &mp, cudaStream_t s) {
+int run_main(polyeval *h, const pe::MainParams &mp, cudaStream_t s, int mode = 0) {
   if (mp.n_items <= 0) return PE_OK;
   if (cudaMemsetAsync(h->counter.p, 0, sizeof(unsigned), s) != cudaSuccess) return PE_ECUDA;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -341,7 +347,7 @@ int run_main(polyeval *h, const pe::MainParams &mp, cudaStream_t s) {
     }
   }
   if (e0 && cudaEventRecord(e0, s) != cudaSuccess) return PE_ECUDA;
-  const Shape sh = shape_for(h, mp.n_items);
+  const Shape sh = shape_for(h, mp.n_items, mode);
   const cudaError_t le = h->wide ? pe::launch_main_wide(mp, sh.warps, sh.smem, sh.grid, s)
                                  : pe::launch_main(h->dd, mp, sh.warps, sh.smem, sh.grid, s);
   if (le != cudaSuccess) return PE_ECUDA;
@@ -535,12 +541,19 @@ int polyeval_many_layout(const polyeval_t *h, int32_t s, int64_t *pt_off, int64_
   return PE_OK;
 }
 
-int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// One single-system evaluation.  chunks > 0 and mode > 0 force the monomial
+// chunk count and the launch shape (used by the autotuner); 0 picks them from
+// the tuned table or the heuristic.
+int eval_single(polyeval *h, const void *points, int64_t P, void *out_f, void *out_J, cudaStream_t s, int chunks,
+                int mode) {
   if (!h || h->batch || P < 0) return PE_EINVAL;
   if (P == 0) return PE_OK;
   if (P > h->max_points) return PE_ERANGE;
   if (!points || (!out_f && h->sys[0].N > 0) || (!out_J && h->sys[0].N > 0)) return PE_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const SysDesc &d = h->sys[0];
   if (table_levels(h, d.emax) > 0) {
     pe::PowerParams pp{};
@@ -566,8 +579,16 @@ int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, voi
   int C = 1;
   const int64_t capacity = static_cast<int64_t>(h->sms) * h->blocks_per_sm_1;
   const size_t per_chunk = outputs_bytes(h, P);
+  if (chunks <= 0 || mode <= 0) {
+    for (const auto &t : h->tuned)
+      if (t.P == P) {
+        if (chunks <= 0) chunks = t.chunks;
+        if (mode <= 0) mode = t.mode;
+      }
+  }
   if (base > 0 && per_chunk > 0) {
-    C = static_cast<int>(std::min<int64_t>(kMaxChunks, std::max<int64_t>(1, capacity / base)));
+    C = chunks > 0 ? std::min(chunks, kMaxChunks)
+                   : static_cast<int>(std::min<int64_t>(kMaxChunks, std::max<int64_t>(1, capacity / base)));
     C = static_cast<int>(std::min<int64_t>(C, 1 + static_cast<int64_t>(h->scratch.bytes / per_chunk)));
   }
   const int64_t f_doubles = static_cast<int64_t>(elem_doubles(h)) * d.N * P;
@@ -578,7 +599,7 @@ int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, voi
   mp.scratch_f = static_cast<double *>(h->scratch.p);
   mp.scratch_J = C > 1 ? mp.scratch_f + static_cast<size_t>(C - 1) * f_doubles : nullptr;
   mp.n_items = base * C;
-  int rc = run_main(h, mp, s);
+  int rc = run_main(h, mp, s, mode);
   if (rc != PE_OK || C == 1) return rc;
   if (pe::launch_combine(h->dd, mp.out_f, mp.out_J, mp.scratch_f, mp.scratch_J, f_doubles, J_doubles, C, s) !=
       cudaSuccess)
@@ -586,6 +607,77 @@ int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, voi
   h->kernels_launched += 2;  // f and J passes
   return PE_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream) {
+  if (!h || h->batch || P < 0) return PE_EINVAL;
+  if (P == 0) return PE_OK;
+  if (P > h->max_points) return PE_ERANGE;
+  if (!points || (!out_f && h->sys[0].N > 0) || (!out_J && h->sys[0].N > 0)) return PE_EINVAL;
+  return eval_single(h, points, P, out_f, out_J, static_cast<cudaStream_t>(stream), 0, 0);
+}
+
+int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream,
+                      int *chunks, int *shape) {
+  if (!h || h->batch || P < 1) return PE_EINVAL;
+  if (P > h->max_points) return PE_ERANGE;
+  if (!points || !out_f || !out_J) return PE_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const SysDesc &d = h->sys[0];
+  const int64_t base = static_cast<int64_t>(d.N) * ((P + pe::kPointsPerWarp - 1) / pe::kPointsPerWarp);
+  const int64_t capacity = static_cast<int64_t>(h->sms) * h->blocks_per_sm_1;
+  const size_t per_chunk = outputs_bytes(h, P);
+  const int max_c = per_chunk ? static_cast<int>(std::min<int64_t>(
+                                    kMaxChunks, 1 + static_cast<int64_t>(h->scratch.bytes / per_chunk)))
+                              : 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return PE_ECUDA;
+  }
+  const bool timing = h->timing;
+  h->timing = false;
+  float best = 0.0f;
+  int best_c = 1, best_m = 2;
+  int rc = PE_OK;
+  for (int C = 1; C <= max_c && rc == PE_OK; C *= 2) {
+    for (int m = 1; m <= 2 && rc == PE_OK; m++) {
+      if (m == 1 && base * C > capacity) continue;  // one wave only when every item is resident
+      rc = eval_single(h, points, P, out_f, out_J, s, C, m);  // warm-up
+      if (rc != PE_OK) break;
+      if (cudaEventRecord(e0, s) != cudaSuccess) rc = PE_ECUDA;
+      for (int r = 0; r < 3 && rc == PE_OK; r++) rc = eval_single(h, points, P, out_f, out_J, s, C, m);
+      if (rc == PE_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+        rc = PE_ECUDA;
+      float ms = 0.0f;
+      if (rc == PE_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = PE_ECUDA;
+      if (rc == PE_OK && (best == 0.0f || ms < best)) {
+        best = ms;
+        best_c = C;
+        best_m = m;
+      }
+    }
+  }
+  h->timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != PE_OK) return rc;
+  bool found = false;
+  for (auto &t : h->tuned)
+    if (t.P == P) {
+      t.chunks = best_c;
+      t.mode = best_m;
+      found = true;
+    }
+  if (!found) h->tuned.push_back(polyeval::Tuned{P, best_c, best_m});
+  if (chunks) *chunks = best_c;
+  if (shape) *shape = best_m;
+  return PE_OK;
+}
+
 
 int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, void *out_J, double *norms, void *stream) {
   if (!h || h->batch) return PE_EINVAL;

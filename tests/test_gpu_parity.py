@@ -442,3 +442,23 @@ def test_integer_path_deterministic_and_close_to_fp64_dd():
     Sf, SJ = scales(s, pts)
     assert normwise_vs(f1.cpu().numpy(), f3.cpu().numpy(), Sf) <= 2 * DD_TOL
     assert normwise_vs(J1.cpu().numpy(), J3.cpu().numpy(), SJ) <= 2 * DD_TOL
+
+
+@pytest.mark.parametrize("prec", ["dd", "ddint"])
+def test_autotune_then_eval(prec):
+    """The autotuner's choice is kept for the point count and gives results
+    within the double-double tolerance of the exact oracle."""
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+    from _util import pe_precision
+
+    s, pts = synth.config(2, n_points=300)
+    ev = pkg.PolyEval(s, pe_precision(prec), max_points=300)
+    x = to_device(pts)
+    chunks, shape = ev.autotune(x)
+    assert chunks in (1, 2, 4, 8) and shape in (1, 2)
+    f, J = ev.eval(x)
+    torch.cuda.synchronize()
+    assert ev.status() == pkg.PE_OK
+    check_exact_oracle(s, pts, f.cpu().numpy(), J.cpu().numpy(), DD_TOL, points_idx=[0, 299], polys=[0, 31])
