@@ -42,7 +42,7 @@ SMS = 152
 DFMA_PER_SM_CLK = 2  # nominal FP64 FMA lanes per SM per clock on GB300
 # DRAM bytes (read + write) of one main-kernel launch on this workload, from the ncu capture
 # summarised in profiles/main_kernel_dd_config2.md; set to None when the kernel changes.
-MAIN_KERNEL_DRAM_BYTES = 4.372992e6 + 4.352e3
+MAIN_KERNEL_DRAM_BYTES = None
 
 
 def env_dist():

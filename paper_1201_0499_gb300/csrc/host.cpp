@@ -139,15 +139,18 @@ struct Cost {
 
 Cost monomial_cost(bool dd, int k, int n2) {
   if (k == 0) return dd ? Cost{10, 10} : Cost{8, 8};
-  const double chain = n2 + (k >= 2 ? 2.0 * k - 3.0 : 0.0);
-  const double fin = k >= 2 ? k : 1.0;
+  // chains: common factor + forward products (n2 + k - 1), backward (k - 2);
+  // every second product of a chain is renormalised
+  const int l1 = n2 + k - 1, l2 = k >= 2 ? k - 2 : 0;
+  const double renorm = l1 / 2 + l2 / 2;
+  const double plain = (l1 + l2) - renorm + (k >= 2 ? k : 1);  // + value and derivative products
   Cost c;
   if (dd) {
-    c.ops = 32 * chain + 26 * fin + 10 * (k + 1) + 6 * n2;
-    c.flops = 44 * chain + 38 * fin + 10 * (k + 1) + 10 * n2;
+    c.ops = 32 * renorm + 26 * plain + 10 * (k + 1) + 6 * n2;
+    c.flops = 44 * renorm + 38 * plain + 10 * (k + 1) + 10 * n2;
   } else {
-    c.ops = 4 * (chain + fin) + 2 * k + 8 + 2 * n2;
-    c.flops = 6 * (chain + fin) + 2 * k + 8 + 2 * n2;
+    c.ops = 4 * (renorm + plain) + 2 * k + 8 + 2 * n2;
+    c.flops = 6 * (renorm + plain) + 2 * k + 8 + 2 * n2;
   }
   return c;
 }
@@ -232,7 +235,17 @@ int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, b
       c.mono_ptr.push_back(static_cast<int32_t>(c.var.size()));
       const pe_cdd &cf = s->coef[t];
       if (dd || wide) {
-        c.coef.insert(c.coef.end(), {cf.re_hi, cf.re_lo, cf.im_hi, cf.im_lo});
+        // renormalised (FastTwoSum after ordering), so the first product of a
+        // chain starts from |lo| <= ulp(hi)/2 whatever the caller passed
+        auto renorm = [](double a, double b, double &hi, double &lo) {
+          const double big = std::fabs(a) >= std::fabs(b) ? a : b, small = std::fabs(a) >= std::fabs(b) ? b : a;
+          hi = big + small;
+          lo = small - (hi - big);
+        };
+        double rh, rl, ih, il;
+        renorm(cf.re_hi, cf.re_lo, rh, rl);
+        renorm(cf.im_hi, cf.im_lo, ih, il);
+        c.coef.insert(c.coef.end(), {rh, rl, ih, il});
       } else {
         c.coef.insert(c.coef.end(), {cf.re_hi, cf.im_hi});
       }

@@ -86,18 +86,27 @@ __device__ void process_item(const MainParams &kp, const Item &it, typename A::V
       continue;
     }
     const uint32_t *vw = kp.var + vb;
+    // Products in a chain are renormalised every second step: one
+    // unnormalised product leaves a low word of a few ulps, which the next
+    // product absorbs at O(u^2) cost; two in a row would let it grow.
+    bool renorm = false;
+    auto chain = [&](V y, const Full &X) {
+      const V r = renorm ? mul_x<A, true>(y, X, sgn) : mul_x<A, false>(y, X, sgn);
+      renorm = !renorm;
+      return r;
+    };
     // Stage 1: G = c * prod_{a_j >= 2} x_{i_j}^(a_j - 1)
     for (int j = 0; j < k; j++) {
       const uint32_t w = __ldg(vw + j);
       const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
-      if (a >= 2) G = mul_x<A, true>(G, A::load_full(a == 2 ? xel(v) : tel(a - 1, v)), sgn);
+      if (a >= 2) G = chain(G, A::load_full(a == 2 ? xel(v) : tel(a - 1, v)));
     }
     // Stage 2, forward: slot j <- G x_{i_1} ... x_{i_j}, j = 0 .. k-2
     V Pc = G;
     for (int j = 0; j < k - 1; j++) {
       smem[j * 32 + lane] = Pc;
       const int v = static_cast<int>(__ldg(vw + j) & 0xffffu);
-      Pc = mul_x<A, true>(Pc, A::load_full(xel(v)), sgn);
+      Pc = chain(Pc, A::load_full(xel(v)));
     }
     // value c x^a = Pc x_{i_k}; derivative by x_{i_k} = a_k Pc
     const uint32_t wl = __ldg(vw + k - 1);
@@ -107,12 +116,13 @@ __device__ void process_item(const MainParams &kp, const Item &it, typename A::V
     accumulate<A>(jel(vl), c, valid, al == 1 ? Pc : A::mul_int(Pc, static_cast<double>(al)));
     // Stage 2, backward: Q = x_{i_{j+2}} ... x_{i_k}; derivative by x_{i_{j+1}} = a_{j+1} slot_j Q
     V Q = A::comp(xl, c);
+    renorm = false;
     for (int j = k - 2; j >= 0; j--) {
       const uint32_t w = __ldg(vw + j);
       const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
       const V D = mul_split<A>(smem[j * 32 + lane], Q, c, sgn);
       accumulate<A>(jel(v), c, valid, a == 1 ? D : A::mul_int(D, static_cast<double>(a)));
-      if (j > 0) Q = mul_x<A, true>(Q, A::load_full(xel(v)), sgn);
+      if (j > 0) Q = chain(Q, A::load_full(xel(v)));
     }
   }
   if (valid) {
