@@ -447,6 +447,29 @@ def main():
                   "points_per_s": job_throughput(world, P, ms_newton),
                   "what": "f, J, LU with partial pivoting per point, x += dx (polyeval_newton)"}
 
+    # the paper's three-kernel design on the same batch (double-double), for comparison
+    paper = None
+    if args.config == CONFIG_INDEX:
+        ev_paper = pkg.PolyEval(wl.system, pkg.PE_DD, max_points=P, flags=pkg.PE_PAPER_KERNELS)
+        xd, fd, Jd = wl.bufs["dd"]
+        for _ in range(args.warmup):
+            ev_paper.eval(xd, fd, Jd)
+        kp = max(min(args.steps, 50), 3)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(kp)]
+        stops = [torch.cuda.Event(enable_timing=True) for _ in range(kp)]
+        for i in range(kp):
+            flush.zero_()
+            starts[i].record(stream)
+            ev_paper.eval(xd, fd, Jd)
+            stops[i].record(stream)
+        torch.cuda.synchronize()
+        ms_paper = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, stops)) / kp, dist)
+        paper = {"ms_per_step": ms_paper, "evals_per_s": job_throughput(world, P, ms_paper),
+                 "fused_fp64_dd_speedup": ms_paper / (ms_per_step if prim == "dd" else legs["dd"]),
+                 "what": "the paper's K1 common factors / K2 Speelpenning + coefficients into zero-padded Mons / "
+                         "K3 one thread per output, complex double-double (PE_PAPER_KERNELS)"}
+        ev_paper.close()
+
     # end to end through the public API: pinned host in, pinned host out
     for _ in range(max(args.warmup, 1)):
         wl.eval_host(prim)
@@ -506,6 +529,7 @@ def main():
                               "sums in double-double" if other == "ddint" else "complex double-double on the FP64 pipe")},
             "fp64_peak_frac": achieved_tflops / peak_nominal,
             "newton_step": newton,
+            "paper_three_kernels": paper,
             "clocks": clocks,
         }
         if cpu is not None:

@@ -76,6 +76,15 @@ extern "C" {
 
 /* ---- flags for polyeval_create / polyeval_create_many / polyeval_validate */
 #define PE_ALLOW_ZERO_COEF 1u /* accept c = 0 (Eq. 1 asks c != 0); for tests */
+/* Evaluate with the paper's own three-kernel design (Sections 3.1-3.3: common
+ * factors to global memory, Speelpenning products and coefficient products
+ * scattered into a zero-padded term array, one thread per output summing m
+ * terms) instead of the fused kernel, for comparison.  PE_DD only; regular
+ * systems only (every polynomial the same number m of monomials, every
+ * monomial the same number k >= 3 of variables) and max_points <= 65535,
+ * else PE_EINVAL.  The term array takes (n^2 + n) m complex double-doubles
+ * per point of max_points. */
+#define PE_PAPER_KERNELS 2u
 
 /* ---- limits ------------------------------------------------------------ */
 #define PE_MAX_VARS 65535 /* n_vars                                        */

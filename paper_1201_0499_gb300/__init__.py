@@ -20,6 +20,7 @@ from ._binding import (  # noqa: F401
     PE_MAX_EXP,
     PE_MAX_VARS,
     PE_OK,
+    PE_PAPER_KERNELS,
     PolyEval,
     PolyEvalError,
     PolyEvalMany,

@@ -30,6 +30,7 @@ PE_F64 = 1
 PE_DD_INT = 2
 
 PE_ALLOW_ZERO_COEF = 1
+PE_PAPER_KERNELS = 2
 
 PE_MAX_VARS = 65535
 PE_MAX_EXP = 256

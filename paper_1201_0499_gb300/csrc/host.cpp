@@ -62,6 +62,8 @@ struct DeviceBuf {
 struct polyeval {
   bool dd = true;     // complex double-double points and outputs (PE_DD, PE_DD_INT)
   bool wide = false;  // products on the integer pipes (PE_DD_INT)
+  bool paper = false; // the paper's three-kernel design (PE_PAPER_KERNELS)
+  int32_t paper_m = 0, paper_k = 0, paper_M = 0;
   bool batch = false;
   int32_t count = 0;
   int64_t max_points = 0;
@@ -81,6 +83,7 @@ struct polyeval {
   DeviceBuf poly_ptr, mono_ptr, var, coef, coef_wide, poly_sys, sysd, perm, items, prefix, table, counter, status;
   DeviceBuf stage_pts, stage_f, stage_J;
   DeviceBuf scratch;  // chunk partial results (single-system handles)
+  DeviceBuf paper_coeffs, paper_cf, paper_mons;  // three-kernel design
   struct Tuned {
     int64_t P;
     int chunks;
@@ -327,6 +330,72 @@ Shape shape_for(const polyeval *h, int64_t n_items, int mode = 0) {
   return Shape{static_cast<int>(std::max<int64_t>(1, std::min(full, need))), h->warps_per_block, h->smem_bytes};
 }
 
+// x * k for a double-double x and a small integer k (TwoProd with an FMA on
+// the high word), renormalised.
+void dd_times_int(double hi, double lo, double k, double &rh, double &rl) {
+  const double p = hi * k;
+  const double e = std::fma(hi, k, -p);
+  const double t = std::fma(lo, k, e);
+  rh = p + t;
+  rl = t - (rh - p);
+}
+
+// The paper's layout: Coeffs holds, for each variable position j of the
+// monomials in S_m order, the coefficients c a_j of the derivatives, then the
+// coefficients c themselves (Section 3.3).
+int setup_paper(polyeval *h, const pe_system *sys, const Compiled &c) {
+  if (!h->dd || h->wide) return PE_EINVAL;
+  const SysDesc &d = h->sys[0];
+  if (d.N < 1 || h->max_points > 65535) return PE_EINVAL;
+  const int64_t M = sys->poly_ptr[d.N];
+  const int64_t m = sys->poly_ptr[1] - sys->poly_ptr[0];
+  if (m < 1) return PE_EINVAL;
+  for (int32_t p = 0; p < d.N; p++)
+    if (sys->poly_ptr[p + 1] - sys->poly_ptr[p] != m) return PE_EINVAL;
+  const int64_t k = sys->mono_ptr[1] - sys->mono_ptr[0];
+  if (k < 3) return PE_EINVAL;
+  for (int64_t t = 0; t < M; t++)
+    if (sys->mono_ptr[t + 1] - sys->mono_ptr[t] != k) return PE_EINVAL;
+  h->paper = true;
+  h->paper_m = static_cast<int32_t>(m);
+  h->paper_k = static_cast<int32_t>(k);
+  h->paper_M = static_cast<int32_t>(M);
+  std::vector<double> co(static_cast<size_t>(k + 1) * M * 4);
+  for (int64_t t = 0; t < M; t++) {
+    const double *cf = &c.coef[static_cast<size_t>(t) * 4];
+    for (int64_t j = 0; j <= k; j++) {
+      const double a = j < k ? static_cast<double>(sys->exp[sys->mono_ptr[t] + j]) : 1.0;
+      double *dst = &co[(static_cast<size_t>(j) * M + t) * 4];
+      dd_times_int(cf[0], cf[1], a, dst[0], dst[1]);
+      dd_times_int(cf[2], cf[3], a, dst[2], dst[3]);
+    }
+  }
+  int rc;
+  const size_t slots = static_cast<size_t>(d.N) * (d.n + 1);
+  if ((rc = h->paper_coeffs.upload(co)) != PE_OK) return rc;
+  if ((rc = h->paper_cf.alloc(static_cast<size_t>(h->max_points) * M * 32)) != PE_OK) return rc;
+  if ((rc = h->paper_mons.alloc(static_cast<size_t>(h->max_points) * m * slots * 32)) != PE_OK) return rc;
+  if (cudaMemset(h->paper_mons.p, 0, h->paper_mons.bytes) != cudaSuccess) return PE_ECUDA;  // zero terms, once
+  int optin = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return PE_ECUDA;
+  const size_t sm1 = 32 * static_cast<size_t>(d.n) * std::max(d.emax - 1, 1);
+  const size_t sm2 = 32 * (static_cast<size_t>(d.n) + static_cast<size_t>(k + 2) * 32);
+  if (sm1 > static_cast<size_t>(optin) || sm2 > static_cast<size_t>(optin)) return PE_ERANGE;
+  if (pe::prepare_paper(static_cast<size_t>(optin), static_cast<size_t>(optin)) != cudaSuccess) return PE_ECUDA;
+  // work of the paper's method per point: K1 powers per block of 32 and k-1
+  // products per monomial, K2 5k-4 products, K3 (n^2+n) m sums; a complex
+  // double-double product is 32 FP64 instructions (44 flops), a sum 10
+  const double blocks = static_cast<double>((M + 31) / 32);
+  const double cm = blocks * d.n * std::max(d.emax - 2, 0) + static_cast<double>(M) * (k - 1) +
+                    static_cast<double>(M) * (5 * k - 4);
+  const double ca = static_cast<double>(slots) * m;
+  h->ops_per_point = 32 * cm + 10 * ca;
+  h->flops_per_point = 44 * cm + 10 * ca;
+  return PE_OK;
+}
+
 pe::MainParams main_params(const polyeval *h) {
   pe::MainParams p{};
   p.poly_ptr = static_cast<const int32_t *>(h->poly_ptr.p);
@@ -420,6 +489,12 @@ int polyeval_create(const pe_system *sys, int precision, uint32_t flags, int64_t
     if ((rc = finish_handle(h, c)) != PE_OK || (rc = h->perm.upload(perm)) != PE_OK) {
       delete h;
       return rc;
+    }
+    if (flags & PE_PAPER_KERNELS) {
+      if ((rc = setup_paper(h, sys, c)) != PE_OK) {
+        delete h;
+        return rc;
+      }
     }
     {
       const size_t per_chunk = outputs_bytes(h, max_points);
@@ -568,6 +643,34 @@ int eval_single(polyeval *h, const void *points, int64_t P, void *out_f, void *o
   if (P > h->max_points) return PE_ERANGE;
   if (!points || (!out_f && h->sys[0].N > 0) || (!out_J && h->sys[0].N > 0)) return PE_EINVAL;
   const SysDesc &d = h->sys[0];
+  if (h->paper) {
+    pe::PaperParams pp{};
+    pp.n = d.n;
+    pp.N = d.N;
+    pp.M = h->paper_M;
+    pp.m = h->paper_m;
+    pp.k = h->paper_k;
+    pp.d = d.emax;
+    pp.P = static_cast<int32_t>(P);
+    pp.var = static_cast<const uint32_t *>(h->var.p);
+    pp.coeffs = static_cast<const double *>(h->paper_coeffs.p);
+    pp.cf = static_cast<double *>(h->paper_cf.p);
+    pp.mons = static_cast<double *>(h->paper_mons.p);
+    pp.points = static_cast<const double *>(points);
+    pp.out_f = static_cast<double *>(out_f);
+    pp.out_J = static_cast<double *>(out_J);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->timing && h->ev_used < kMaxTimingEvents) {
+      e0 = h->ev[2 * h->ev_used];
+      e1 = h->ev[2 * h->ev_used + 1];
+      h->ev_used++;
+    }
+    if (e0 && cudaEventRecord(e0, s) != cudaSuccess) return PE_ECUDA;
+    if (pe::launch_paper(pp, s) != cudaSuccess) return PE_ECUDA;
+    if (e1 && cudaEventRecord(e1, s) != cudaSuccess) return PE_ECUDA;
+    h->kernels_launched += 3;
+    return PE_OK;
+  }
   if (table_levels(h, d.emax) > 0) {
     pe::PowerParams pp{};
     pp.sys = static_cast<const SysDesc *>(h->sysd.p);

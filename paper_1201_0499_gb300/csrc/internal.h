@@ -93,6 +93,23 @@ struct NewtonParams {
 };
 cudaError_t launch_newton(bool dd, const NewtonParams &p, cudaStream_t s);
 
+// The paper's three-kernel design (three_kernel.cu), complex double-double.
+struct PaperParams {
+  int32_t n, N;      // variables, polynomials
+  int32_t M, m, k;   // monomials (N m), monomials per polynomial, variables per monomial
+  int32_t d;         // largest exponent
+  int32_t P;         // points
+  const uint32_t *var;    // [M][k] position | exponent << 16
+  const double *coeffs;   // [k + 1][M] complex dd: c a_j (portion j), c (portion k)
+  double *cf;             // [P][M] common factors (K1 -> K2)
+  double *mons;           // [P][m][N (n + 1)] terms (K2 -> K3)
+  const double *points;   // [n][P]
+  double *out_f;          // [N][P]
+  double *out_J;          // [N][n][P]
+};
+cudaError_t launch_paper(const PaperParams &p, cudaStream_t s);
+cudaError_t prepare_paper(size_t smem_k1, size_t smem_k2);
+
 // Integer-pipe evaluation (kernels_wide.cu): 128-bit block floating point
 // products, double-double sums.  Table entries and coefficients are 48 bytes.
 constexpr int kWideBytes = 48;
