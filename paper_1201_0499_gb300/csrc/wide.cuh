@@ -81,23 +81,19 @@ __device__ __forceinline__ WV component(const WF &x, int c) {
 
 __device__ __forceinline__ bool is_zero(const Mag &a) { return (a.w0 | a.w1 | a.w2 | a.w3) == 0u; }
 
-// Top 128 bits of the 256-bit product a*b, columns 0..2 of the partial
-// products dropped (result low by at most 4 units).
+// Top 128 bits of the 256-bit product a*b.  Columns 0..2 of the partial
+// products are dropped and column 3 contributes only its high words, so the
+// result is low by at most 7 units in its last place.
 __device__ __forceinline__ Mag mul_hi(const Mag &a, const Mag &b) {
   uint32_t c1, c2, c3, c4;
   asm("{\n\t"
-      ".reg .u32 c0;\n\t"
-      // column 3: a0b3 + a1b2 + a2b1 + a3b0 into (c0, c1, c2)
-      "mul.lo.u32      c0, %4, %11;\n\t"
+      // column 3, high words: hi(a0b3) + hi(a1b2) + hi(a2b1) + hi(a3b0) into (c1, c2)
       "mul.hi.u32      %0, %4, %11;\n\t"
-      "mad.lo.cc.u32   c0, %5, %10, c0;\n\t"
-      "madc.hi.cc.u32  %0, %5, %10, %0;\n\t"
+      "mad.hi.cc.u32   %0, %5, %10, %0;\n\t"
       "addc.u32        %1, 0, 0;\n\t"
-      "mad.lo.cc.u32   c0, %6, %9, c0;\n\t"
-      "madc.hi.cc.u32  %0, %6, %9, %0;\n\t"
+      "mad.hi.cc.u32   %0, %6, %9, %0;\n\t"
       "addc.u32        %1, %1, 0;\n\t"
-      "mad.lo.cc.u32   c0, %7, %8, c0;\n\t"
-      "madc.hi.cc.u32  %0, %7, %8, %0;\n\t"
+      "mad.hi.cc.u32   %0, %7, %8, %0;\n\t"
       "addc.u32        %1, %1, 0;\n\t"
       // column 4: a1b3 + a2b2 + a3b1 into (c1, c2, c3)
       "mad.lo.cc.u32   %0, %5, %11, %0;\n\t"
@@ -214,6 +210,16 @@ __device__ __forceinline__ Mag shfl_xor_mag(const Mag &a, int m) {
 // Normalise a lane-pair value: the larger magnitude of the pair to
 // [2^125, 2^126), both lanes shifted alike; zero pairs get kZeroExp.
 __device__ __forceinline__ WV normalize_pair(const WV &v) {
+  // usual case: both leading bits in the top limb, a left shift below 32
+  const int lz3 = __clz(static_cast<int>(v.m.w3));
+  const int lz3p = __shfl_xor_sync(0xffffffffu, lz3, 1);
+  const int z3 = min(lz3, lz3p);
+  if (__all_sync(0xffffffffu, z3 >= 2 && z3 < 32)) {
+    const int sh = z3 - 2;
+    return WV{Mag{v.m.w0 << sh, __funnelshift_l(v.m.w0, v.m.w1, sh), __funnelshift_l(v.m.w1, v.m.w2, sh),
+                  __funnelshift_l(v.m.w2, v.m.w3, sh)},
+              v.s, v.e - sh};
+  }
   const int lz = clz128(v.m);
   const int lzp = __shfl_xor_sync(0xffffffffu, lz, 1);
   const int z = min(lz, lzp);
@@ -294,7 +300,28 @@ __device__ __forceinline__ unsigned long long bits53(const Mag &m, int top) {
 }
 
 // A lane value as a double-double (truncated to 106 bits; not renormalised).
+// Fast path for a leading bit in the top limb: the value shifted so that the
+// leading bit is bit 127 gives the 53 bits of the high word and the next 53
+// bits of the low word directly.
+__device__ __forceinline__ dd to_dd_general(const WV &v);
 __device__ __forceinline__ dd to_dd(const WV &v) {
+  if (v.m.w3 == 0u) return to_dd_general(v);
+  const int s = __clz(static_cast<int>(v.m.w3));  // 0..31
+  const uint32_t t3 = __funnelshift_l(v.m.w2, v.m.w3, s), t2 = __funnelshift_l(v.m.w1, v.m.w2, s);
+  const uint32_t t1 = __funnelshift_l(v.m.w0, v.m.w1, s), t0 = v.m.w0 << s;
+  const unsigned long long top64 = (static_cast<unsigned long long>(t3) << 32) | t2;
+  const unsigned long long low64 = (static_cast<unsigned long long>(t1) << 32) | t0;
+  const unsigned long long hs = top64 >> 11;                              // bits 127..75
+  const unsigned long long ls = ((top64 & 0x7ffULL) << 42) | (low64 >> 22);  // bits 74..22
+  // value = m 2^e with bit 127 of (m << s) the leading bit: hi lsb at 2^(e + 75 - s)
+  const double hi = make_double(hs, v.e + 75 - s, v.s);
+  if (ls == 0ULL) return dd{hi, 0.0};
+  const int lz = __clzll(static_cast<long long>(ls)) - 11;  // leading zeros of the 53-bit field
+  const double lo = make_double(ls << lz, v.e + 22 - s - lz, v.s);
+  return dd{hi, lo};
+}
+
+__device__ __forceinline__ dd to_dd_general(const WV &v) {
   const int lz = clz128(v.m);
   if (lz == 128) return dd{0.0, 0.0};
   const int top = 127 - lz;
