@@ -199,10 +199,20 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+QD_SEED = synth.SEED_BASE + 500  # lower parts of the quad-double copy of the workload
+
+
+def buf_fmt(prec):
+    """Buffer set a precision reads and writes."""
+    return {"f64": "f64", "qd": "qd"}.get(prec, "dd")
+
+
 class Workload:
     """The batch one step evaluates, with an evaluator per precision
     ("dd": double-double on the FP64 pipe, "ddint": integer-pipe products,
-    "f64": complex double), device buffers and pinned host buffers."""
+    "f64": complex double, "qd": quad-double on the integer pipes, on the same
+    data widened by two random lower parts), device buffers and pinned host
+    buffers."""
 
     def __init__(self, cfg, rank, dev):
         import torch
@@ -210,21 +220,29 @@ class Workload:
         import paper_1201_0499_gb300 as pkg
 
         self.pkg, self.torch, self.dev, self.cfg = pkg, torch, dev, cfg
-        codes = {"dd": pkg.PE_DD, "ddint": pkg.PE_DD_INT, "f64": pkg.PE_F64}
+        codes = {"dd": pkg.PE_DD, "ddint": pkg.PE_DD_INT, "f64": pkg.PE_F64, "qd": pkg.PE_QD_INT}
+        rng = np.random.Generator(np.random.PCG64(QD_SEED))
+
+        def inputs(fmt, system, p):
+            if fmt == "f64":
+                return system.as_fp64(), np.ascontiguousarray(p[..., [0, 2]])
+            if fmt == "qd":
+                return system.to_qd(QD_SEED + 1), synth.widen_qd(rng, p)
+            return system, p
+
         if cfg == 4:
             systems, pts = synth.config(4)
             self.text = synth.CONFIG_TEXT[4] + ", one launch"
             npts = [p.shape[1] for p in pts]
-            self.ev = {k: pkg.PolyEvalMany(systems if k != "f64" else [s.as_fp64() for s in systems], npts, code)
-                       for k, code in codes.items()}
+            self.ev, self.bufs = {}, {}
+            for k, code in codes.items():
+                ins = [inputs(buf_fmt(k), s_, p_) for s_, p_ in zip(systems, pts)]
+                self.ev[k] = pkg.PolyEvalMany([a for a, _ in ins], npts, code)
+                if k in ("dd", "f64", "qd"):
+                    b = self.ev[k].buffers(dev)
+                    self.ev[k].pack_points([torch.from_numpy(np.ascontiguousarray(b_)) for _, b_ in ins], b[0])
+                    self.bufs[k] = b
             self.points = sum(npts)
-            self.bufs = {}
-            for fmt in ("dd", "f64"):
-                ev = self.ev[fmt]
-                b = ev.buffers(dev)
-                ev.pack_points([torch.from_numpy(p if fmt == "dd" else np.ascontiguousarray(p[..., [0, 2]]))
-                                for p in pts], b[0])
-                self.bufs[fmt] = b
             self.host = [t.cpu().pin_memory() for t in self.bufs["dd"]]
             self.system, self.pts = systems, pts
         else:
@@ -239,14 +257,16 @@ class Workload:
                 self.text = synth.CONFIG_TEXT[cfg]
             n, N = system.n_vars, system.n_polys
             self.system, self.pts, self.points = system, pts, P
-            self.ev = {k: pkg.PolyEval(system if k != "f64" else system.as_fp64(), code, max_points=P)
-                       for k, code in codes.items()}
-            self.bufs = {}
-            for fmt in ("dd", "f64"):
-                c = 4 if fmt == "dd" else 2
-                x = torch.from_numpy(pts if fmt == "dd" else np.ascontiguousarray(pts[..., [0, 2]])).to(dev)
-                self.bufs[fmt] = (x, torch.empty((N, P, c), dtype=torch.float64, device=dev),
-                                  torch.empty((N, n, P, c), dtype=torch.float64, device=dev))
+            self.ev, self.bufs = {}, {}
+            for k, code in codes.items():
+                fmt = buf_fmt(k)
+                sk, pk = inputs(fmt, system, pts)
+                self.ev[k] = pkg.PolyEval(sk, code, max_points=P)
+                if k == fmt:
+                    c = pk.shape[-1]
+                    self.bufs[fmt] = (torch.from_numpy(pk).to(dev),
+                                      torch.empty((N, P, c), dtype=torch.float64, device=dev),
+                                      torch.empty((N, n, P, c), dtype=torch.float64, device=dev))
             self.host = [torch.from_numpy(pts).pin_memory(), torch.empty((N, P, 4), dtype=torch.float64).pin_memory(),
                          torch.empty((N, n, P, 4), dtype=torch.float64).pin_memory()]
         self.h2d_bytes = int(self.host[0].numel() * 8)
@@ -256,7 +276,7 @@ class Workload:
         return self.ev[prec].handle
 
     def eval(self, prec):
-        x, f, J = self.bufs["f64" if prec == "f64" else "dd"]
+        x, f, J = self.bufs[buf_fmt(prec)]
         if self.cfg == 4:
             self.ev[prec].eval_buffers(x, f, J)
         else:
@@ -328,8 +348,8 @@ def main():
     tuned = {}
     if not args.no_autotune and args.config != 4:
         # pick the launch per precision on this batch, before any timed step
-        for prec in ("dd", "ddint", "f64"):
-            x, f, J = wl.bufs["f64" if prec == "f64" else "dd"]
+        for prec in ("dd", "ddint", "f64", "qd"):
+            x, f, J = wl.bufs[buf_fmt(prec)]
             tuned[prec] = pkg.polyeval_autotune(wl.handle(prec), x, wl.points, f, J, stream)
         torch.cuda.synchronize()
 
@@ -355,7 +375,7 @@ def main():
     if args.graph:
         # capture one evaluation per precision; the library call queues only
         # kernels and a memset on the capturing stream
-        for prec in ("dd", "ddint", "f64"):
+        for prec in ("dd", "ddint", "f64", "qd"):
             wl.eval(prec)
             torch.cuda.synchronize()
             g = torch.cuda.CUDAGraph()
@@ -414,7 +434,7 @@ def main():
 
     # complex double path and the other double-double path on the same workload, same harness
     legs = {}
-    for leg in ("f64", other):
+    for leg in ("f64", other, "qd"):
         for _ in range(args.warmup):
             step(leg)
         kl = max(args.steps, 10) if args.config == CONFIG_INDEX else args.steps
@@ -528,6 +548,11 @@ def main():
                 "speedup_vs_fp64_dd": (ms_per_step / legs[other]) if other == "ddint" else (legs[other] / ms_per_step),
                 "precision": ("complex double-double in/out, products in 128-bit integer block floating point, "
                               "sums in double-double" if other == "ddint" else "complex double-double on the FP64 pipe")},
+            "qd_int_path": {
+                "evals_per_s": job_throughput(world, P, legs["qd"]), "ms_per_step": legs["qd"],
+                "time_vs_fp64_dd": legs["qd"] / (ms_per_step if prim == "dd" else legs["dd"]),
+                "precision": "complex quad-double in/out (the same data with two random lower parts), products in "
+                             "256-bit integer block floating point, sums in 224-bit integer accumulators"},
             "fp64_peak_frac": achieved_tflops / peak_nominal,
             "newton_step": newton,
             "paper_three_kernels": paper,

@@ -1,7 +1,7 @@
 /*
  * polyeval -- evaluation of a sparse polynomial system and its full Jacobian
- * at many points on one GB300 GPU (sm_103a), in complex double-double or in
- * complex double precision.
+ * at many points on one GB300 GPU (sm_103a), in complex double-double,
+ * complex quad-double or complex double precision.
  *
  * The method is the one of Verschelde & Yoffe, "Evaluating polynomials in
  * several variables and their derivatives on a GPU computing processor":
@@ -26,6 +26,8 @@
  * Data layouts (structure of arrays, point index fastest):
  *   - A complex double-double (pe_cdd) is 4 doubles: re_hi, re_lo, im_hi,
  *     im_lo; the value is (re_hi + re_lo) + i (im_hi + im_lo).  A complex
+ *     quad-double (pe_cqd) is 8 doubles: re[0..3], im[0..3]; the value is
+ *     (re[0] + re[1] + re[2] + re[3]) + i (im[0] + ... + im[3]).  A complex
  *     double (pe_c64) is 2 doubles: re, im.
  *   - points: [n_vars][P] entries (entry (v, q) at index v * P + q).
  *   - out_f : [n_polys][P]          (f_p at point q at index p * P + q).
@@ -36,8 +38,9 @@
  *
  * Accuracy (normwise, against the exact result, relative to the same sum
  * over absolute values: sum |c| |x^a| for f, sum |c| a_i |x^(a - e_i)| for
- * J): <= 1e-28 for PE_DD and <= 1e-13 for PE_F64 on the workloads this
- * library is tested on; see the tests for the exact cases.
+ * J): <= 1e-28 for PE_DD and PE_DD_INT, <= 1e-60 for PE_QD_INT and <= 1e-13
+ * for PE_F64 on the workloads this library is tested on; see the tests for
+ * the exact cases.
  */
 #ifndef POLYEVAL_H
 #define POLYEVAL_H
@@ -73,6 +76,16 @@ extern "C" {
  * and, on GB300 where FP64 issues about 36x slower than integer multiply-add,
  * faster. */
 #define PE_DD_INT 2
+/* Complex quad-double in and out (pe_cqd), the precision of the QD library
+ * the paper's CPU code uses (Section 1).  Products in complex block floating
+ * point with 256-bit integer mantissas (error about 2^-246 per product
+ * relative to the operands' magnitudes); every sum in a 224-bit integer
+ * accumulator per output component, kept in place in the output arrays and
+ * rounded to quad-double (each part the nearest double to what the parts
+ * before it leave) by a final pass.  No FP64 arithmetic.  Coefficients come
+ * from pe_system.coef_qd, or from coef (lower parts zero) when coef_qd is
+ * NULL.  polyeval_newton and PE_PAPER_KERNELS reject this precision. */
+#define PE_QD_INT 3
 
 /* ---- flags for polyeval_create / polyeval_create_many / polyeval_validate */
 #define PE_ALLOW_ZERO_COEF 1u /* accept c = 0 (Eq. 1 asks c != 0); for tests */
@@ -98,6 +111,10 @@ typedef struct {
   double re, im;
 } pe_c64;
 
+typedef struct {
+  double re[4], im[4];
+} pe_cqd;
+
 /*
  * A polynomial system in compressed rows (Section 2, Eq. 1; the monomial
  * order of Section 3.3: the monomials of polynomial 0, then of polynomial 1,
@@ -114,7 +131,10 @@ typedef struct {
  *              monomial (i_1 < i_2 < ... < i_k)
  *   exp        exponent 1 <= a <= PE_MAX_EXP
  *   coef       [M] coefficients, nonzero and finite.  For PE_F64 only the
- *              high words are read.
+ *              high words are read.  May be NULL when coef_qd is given and the
+ *              precision is PE_QD_INT.
+ *   coef_qd    [M] quad-double coefficients, nonzero and finite, or NULL.
+ *              Read only by PE_QD_INT (which then ignores coef).
  */
 typedef struct {
   int32_t n_vars;
@@ -124,12 +144,14 @@ typedef struct {
   const int32_t *pos;
   const int32_t *exp;
   const pe_cdd *coef;
+  const pe_cqd *coef_qd;
 } pe_system;
 
 typedef struct polyeval polyeval_t;
 
 /*
- * Check a system on the host only (no CUDA call).  Returns PE_OK, PE_EINVAL
+ * Check a system on the host only (no CUDA call).  The coefficients checked
+ * are coef, or coef_qd when coef is NULL.  Returns PE_OK, PE_EINVAL
  * (null pointer, n_vars < 1, n_polys < 0, offsets not starting at 0 or
  * decreasing, pos out of range / not strictly increasing, exponent < 1,
  * zero or non-finite coefficient without PE_ALLOW_ZERO_COEF) or PE_ERANGE
@@ -141,7 +163,7 @@ PE_API int polyeval_validate(const pe_system *sys, uint32_t flags);
 /*
  * Compile one system for evaluation (Section 2 format -> device metadata).
  *   sys         host system, copied; the caller may free it on return
- *   precision   PE_DD, PE_F64 or PE_DD_INT
+ *   precision   PE_DD, PE_F64, PE_DD_INT or PE_QD_INT
  *   flags       PE_ALLOW_ZERO_COEF or 0
  *   max_points  largest P any later polyeval_eval call will pass (>= 1);
  *               sizes the table of powers (Section 3.1) kept on the device
@@ -156,7 +178,8 @@ PE_API int polyeval_create(const pe_system *sys, int precision, uint32_t flags, 
 
 /*
  * Evaluate f and J at P points (Sections 3.1-3.3).
- *   points  device, [n_vars][P] pe_cdd (PE_DD, PE_DD_INT) or pe_c64 (PE_F64)
+ *   points  device, [n_vars][P] pe_cdd (PE_DD, PE_DD_INT), pe_cqd (PE_QD_INT)
+ *           or pe_c64 (PE_F64)
  *   P       number of points, 0 <= P <= max_points (0 returns PE_OK at once)
  *   out_f   device, [n_polys][P] of the same element type
  *   out_J   device, [n_polys][n_vars][P] of the same element type
@@ -166,7 +189,9 @@ PE_API int polyeval_create(const pe_system *sys, int precision, uint32_t flags, 
  * the call has few (polynomial, tile of 16 points) work items, each
  * polynomial's monomials are split into up to 8 chunks whose partial sums go
  * to handle-owned scratch (at most 256 MiB, sized at create) and are added
- * by a final kernel.  Calls on one handle must not overlap on the GPU (they
+ * by a final kernel (for PE_QD_INT the final kernel always runs: it rounds
+ * the integer sums in the outputs to quad-double, so the outputs hold
+ * intermediate sums until it completes).  Calls on one handle must not overlap on the GPU (they
  * share the power table, the scratch and the work counter).  Errors: PE_EINVAL (null handle/pointer with P > 0),
  * PE_ERANGE (P > max_points), PE_ECUDA (launch failure).
  */
@@ -203,8 +228,9 @@ PE_API int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void 
  *   stream  as polyeval_eval
  * The solve is LU with partial pivoting per point (pivot of largest modulus)
  * in the handle's precision (double-double for PE_DD and PE_DD_INT, double
- * for PE_F64), one lane pair per point.  Allocates nothing.  Errors: those of
- * polyeval_eval; PE_EINVAL for a batch handle or a non-square system.
+ * for PE_F64), one warp per point.  Allocates nothing.  Errors: those of
+ * polyeval_eval; PE_EINVAL for a batch handle, a non-square system or a
+ * PE_QD_INT handle.
  */
 PE_API int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, void *out_J, double *norms,
                            void *stream);
@@ -237,7 +263,7 @@ PE_API int polyeval_create_many(const pe_system *systems, int32_t count, int pre
  * pe_c64): its points start at points + *pt_off and are laid out
  * [n_s][P_s]; its f at out_f + *f_off ([N_s][P_s]); its J at out_J + *J_off
  * ([N_s][n_s][P_s]).  Any of the output pointers may be NULL.  With s = count
- * the offsets are the total sizes.  Errors: PE_EINVAL (not a batch handle,
+ * the offsets are the total sizes (elements are pe_cqd for PE_QD_INT).  Errors: PE_EINVAL (not a batch handle,
  * s out of range).
  */
 PE_API int polyeval_many_layout(const polyeval_t *h, int32_t s, int64_t *pt_off, int64_t *f_off, int64_t *J_off);
@@ -255,7 +281,8 @@ PE_API int polyeval_eval_many(polyeval_t *h, const void *points, void *out_f, vo
  * whole polyeval_eval_many):
  *   fp64_ops    double-precision instructions (add, mul, fma) the method
  *               executes, counted from the compiled system (for PE_DD_INT:
- *               those of its double-double sums)
+ *               those of its double-double sums; 0 for PE_QD_INT, which
+ *               has none)
  *   fp64_flops  the same with an fma counted as 2 flops
  * Either pointer may be NULL.
  */

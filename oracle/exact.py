@@ -12,8 +12,8 @@ It evaluates the plain definitions of Section 2, Eq. (1) of Verschelde & Yoffe:
 term by term, for every point, with no common factors, no Speelpenning
 products and no reordering: each term is the product written out.
 
-Every input is a double or a double-double, hence a dyadic rational, so the
-arithmetic here is exact: a complex number is held as (A + iB) * 2**E with
+Every input is a double, a double-double or a quad-double (a sum of two or
+four doubles), hence a dyadic rational, so the arithmetic here is exact: a complex number is held as (A + iB) * 2**E with
 Python integers A, B, E.  Nothing is rounded until an error is measured.
 
 The normwise error of a computed output z against the exact value z* is
@@ -44,16 +44,23 @@ def dyadic(x: float) -> Tuple[int, int]:
 
 def real_dd(hi: float, lo: float) -> Tuple[int, int]:
     """hi + lo exactly, as (M, E)."""
-    mh, eh = dyadic(hi)
-    ml, el = dyadic(lo)
-    e = min(eh, el)
-    return (mh << (eh - e)) + (ml << (el - e)), e
+    return real_sum((hi, lo))
+
+
+def real_sum(parts: Sequence[float]) -> Tuple[int, int]:
+    """The exact sum of any doubles, as (M, E)."""
+    ds = [dyadic(float(x)) for x in parts]
+    e = min(d[1] for d in ds)
+    return sum(m << (x - e) for m, x in ds), e
 
 
 def cx_from_dd(v: Sequence[float]):
-    """Complex double-double (re_hi, re_lo, im_hi, im_lo) exactly."""
-    a, ea = real_dd(v[0], v[1])
-    b, eb = real_dd(v[2], v[3])
+    """A complex multi-double exactly: 4 values (re_hi, re_lo, im_hi, im_lo)
+    for a double-double, 8 (re0..re3, im0..im3) for a quad-double; each
+    component is the exact sum of its parts."""
+    w = len(v) // 2
+    a, ea = real_sum(v[:w])
+    b, eb = real_sum(v[w:2 * w])
     e = min(ea, eb)
     return (a << (ea - e), b << (eb - e), e)
 
@@ -154,7 +161,8 @@ class _LazyPowers:
 
 
 def evaluate_point(system, pts, q: int, polys=None):
-    """Exact f_p and row J[p, :] at point index q of ``pts`` (float64 [n, P, 4]).
+    """Exact f_p and row J[p, :] at point index q of ``pts`` (float64 [n, P, 4]
+    or, for quad-double points, [n, P, 8]).
 
     Returns (f, J): f[p] an exact complex; J[p] a dict {i: exact complex} of
     the variables that occur in polynomial p (absent entries are exactly 0).
@@ -188,16 +196,18 @@ def evaluate_point(system, pts, q: int, polys=None):
 def scales_point(system, pts, q: int, polys=None):
     """Normwise scales at point q: S_f[p] = sum |c| |x|^a and
     S_J[p][i] = sum |c| a_i |x_i|^(a_i - 1) prod_{j != i} |x_j|^{a_j}, in float64."""
+    wp = pts.shape[-1] // 2  # leading part of the imaginary component
+    wc = system.coef.shape[-1] // 2
     ax = {}
     for v in set(system.pos.tolist()):
-        ax[v] = math.hypot(pts[v, q, 0], pts[v, q, 2])
+        ax[v] = math.hypot(pts[v, q, 0], pts[v, q, wp])
     Sf, SJ = {}, {}
     for p in (range(system.n_polys) if polys is None else polys):
         sf = 0.0
         sj = {}
         for t in range(int(system.poly_ptr[p]), int(system.poly_ptr[p + 1])):
             pos, exp = system.monomial(t)
-            ac = math.hypot(system.coef[t, 0], system.coef[t, 2])
+            ac = math.hypot(system.coef[t, 0], system.coef[t, wc])
             term = ac
             for v, a in zip(pos, exp):
                 term *= ax[v] ** a
@@ -213,7 +223,8 @@ def scales_point(system, pts, q: int, polys=None):
 
 
 def normwise_error(got: Sequence[float], exact, scale: float) -> float:
-    """|got - exact| / scale; got is a complex double-double (4 floats).
+    """|got - exact| / scale; got is a complex double-double (4 floats) or
+    quad-double (8 floats).
     When the scale is 0 (no term contributes) the value must be exactly 0:
     returns 0 if it is and inf otherwise."""
     if not all(math.isfinite(v) for v in got):
@@ -227,8 +238,8 @@ def normwise_error(got: Sequence[float], exact, scale: float) -> float:
 def max_errors(system, pts, out_f, out_J, points_idx: Sequence[int], polys=None):
     """Largest normwise errors (f, J) of computed outputs at the given points.
 
-    out_f: float64 [N, P, 4]; out_J: float64 [N, n, P, 4] (structure of
-    arrays, point-minor).  Entries J[p, i] for variables absent from
+    out_f: float64 [N, P, c]; out_J: float64 [N, n, P, c] (structure of
+    arrays, point-minor), c = 4 (double-double) or 8 (quad-double).  Entries J[p, i] for variables absent from
     polynomial p must be exactly zero."""
     ef = ej = 0.0
     n = system.n_vars

@@ -21,6 +21,7 @@ from ._binding import (  # noqa: F401
     PE_MAX_VARS,
     PE_OK,
     PE_PAPER_KERNELS,
+    PE_QD_INT,
     PolyEval,
     PolyEvalError,
     PolyEvalMany,

@@ -28,6 +28,7 @@ PE_EDEVICE = -5
 PE_DD = 0
 PE_F64 = 1
 PE_DD_INT = 2
+PE_QD_INT = 3
 
 PE_ALLOW_ZERO_COEF = 1
 PE_PAPER_KERNELS = 2
@@ -55,6 +56,7 @@ class pe_system(ctypes.Structure):
         ("pos", ctypes.c_void_p),
         ("exp", ctypes.c_void_p),
         ("coef", ctypes.c_void_p),
+        ("coef_qd", ctypes.c_void_p),
     ]
 
 
@@ -133,18 +135,28 @@ def _check(rc: int, where: str):
 
 
 class _Packed:
-    """A pe_system plus the numpy arrays it points into."""
+    """A pe_system plus the numpy arrays it points into.  ``system.coef`` is
+    [M, 4] (complex double-double) or [M, 8] (complex quad-double: passed as
+    coef_qd, with its leading two parts per component as coef)."""
 
     def __init__(self, system):
+        coef = np.asarray(system.coef, dtype=np.float64)
+        coef = coef.reshape(-1, coef.shape[-1] if coef.ndim == 2 and coef.shape[-1] in (4, 8) else 4)
+        qd = None
+        if coef.shape[1] == 8:
+            qd = np.ascontiguousarray(coef)
+            coef = coef[:, [0, 1, 4, 5]]
         self.arrays = [
             np.ascontiguousarray(system.poly_ptr, dtype=np.int64),
             np.ascontiguousarray(system.mono_ptr, dtype=np.int64),
             np.ascontiguousarray(system.pos, dtype=np.int32),
             np.ascontiguousarray(system.exp, dtype=np.int32),
-            np.ascontiguousarray(system.coef, dtype=np.float64).reshape(-1, 4),
+            np.ascontiguousarray(coef),
         ]
+        self.qd = qd
         a = self.arrays
-        self.struct = pe_system(int(system.n_vars), int(system.n_polys), *[x.ctypes.data for x in a])
+        self.struct = pe_system(int(system.n_vars), int(system.n_polys), *[x.ctypes.data for x in a],
+                                qd.ctypes.data if qd is not None else None)
 
 
 # ----------------------------------------------------------------------------
@@ -265,13 +277,14 @@ def polyeval_eval_noalloc(dev_sys: pe_system, max_k: int, max_exp: int, points, 
 # ----------------------------------------------------------------------------
 
 def _elem(precision: int) -> int:
-    return 2 if precision == PE_F64 else 4
+    """Doubles per complex element of a precision."""
+    return 2 if precision == PE_F64 else 8 if precision == PE_QD_INT else 4
 
 
 class PolyEval:
     """One compiled system.  ``eval(points)`` takes a float64 CUDA tensor of
-    shape [n, P, 4] (double-double) or [n, P, 2] (double) and returns
-    (f [N, P, c], J [N, n, P, c]) as new CUDA tensors."""
+    shape [n, P, c] -- c = 4 (double-double), 8 (quad-double) or 2 (double)
+    -- and returns (f [N, P, c], J [N, n, P, c]) as new CUDA tensors."""
 
     def __init__(self, system, precision: int = PE_DD, max_points: int = 1, flags: int = 0):
         self.n_vars = int(system.n_vars)
@@ -362,14 +375,16 @@ class PolyEvalMany:
                 torch.empty((tot[2], c), dtype=torch.float64, device=device))
 
     def pack_points(self, points_list, buf):
+        c = _elem(self.precision)
         for (n, N, P), (po, _fo, _jo), x in zip(self.shapes, self.layout, points_list):
-            buf[po:po + n * P].view(n, P, -1).copy_(x)
+            buf[po:po + n * P].view(n, P, c).copy_(x)
 
     def views(self, out_f, out_J):
+        c = _elem(self.precision)
         fs, Js = [], []
         for (n, N, P), (_po, fo, jo) in zip(self.shapes, self.layout):
-            fs.append(out_f[fo:fo + N * P].view(N, P, -1))
-            Js.append(out_J[jo:jo + N * n * P].view(N, n, P, -1))
+            fs.append(out_f[fo:fo + N * P].view(N, P, c))
+            Js.append(out_J[jo:jo + N * n * P].view(N, n, P, c))
         return fs, Js
 
     def eval_buffers(self, pts_buf, f_buf, J_buf, stream=None):

@@ -27,6 +27,8 @@ constexpr size_t kScratchBudget = size_t{256} << 20;
 // Integer path: above this many prefix slots per lane a warp's slots no longer
 // leave room for 16 warps per SM, and only every second slot is stored.
 constexpr int kWideSlotsFull = 20;
+// Quad-double path: the same with its 36-byte slots (16 warps per SM).
+constexpr int kQdSlotsFull = 12;
 
 struct DeviceBuf {
   void *p = nullptr;
@@ -62,6 +64,7 @@ struct DeviceBuf {
 struct polyeval {
   bool dd = true;     // complex double-double points and outputs (PE_DD, PE_DD_INT)
   bool wide = false;  // products on the integer pipes (PE_DD_INT)
+  bool qd = false;    // complex quad-double points and outputs, all on the integer pipes (PE_QD_INT)
   bool paper = false; // the paper's three-kernel design (PE_PAPER_KERNELS)
   int32_t paper_m = 0, paper_k = 0, paper_M = 0;
   bool batch = false;
@@ -77,6 +80,7 @@ struct polyeval {
   int blocks_per_sm_1 = 1;  // occupancy with one warp per block
   size_t smem_per_warp = 0;
   int64_t n_items_batch = 0;
+  int64_t f_total_batch = 0, J_total_batch = 0;  // batch: complex entries of all f and J
   int64_t power_total_batch = 0;
   double ops_per_point = 0.0, flops_per_point = 0.0;  // single: per point; batch: per whole evaluation
   // device memory
@@ -103,19 +107,26 @@ struct polyeval {
 
 namespace {
 
-int elem_doubles(const polyeval *h) { return h->dd ? 4 : 2; }
+int elem_doubles(const polyeval *h) { return h->qd ? 8 : h->dd ? 4 : 2; }
+
+// Products on the integer pipes (block-format table and coefficients).
+bool block_format(const polyeval *h) { return h->wide || h->qd; }
 
 // Table of powers: entries per (variable, point) and bytes per entry.  The
 // double-double and double tables hold x^2 .. x^(emax-1); the block-format
 // table also holds x itself (entry 1).
 int64_t table_levels(const polyeval *h, int emax) {
-  return h->wide ? std::max(emax - 1, 1) : std::max(emax - 2, 0);
+  return block_format(h) ? std::max(emax - 1, 1) : std::max(emax - 2, 0);
 }
-size_t table_entry_bytes(const polyeval *h) { return h->wide ? pe::kWideBytes : elem_doubles(h) * sizeof(double); }
+size_t table_entry_bytes(const polyeval *h) {
+  return h->qd ? pe::kQdBytes : h->wide ? pe::kWideBytes : elem_doubles(h) * sizeof(double);
+}
 
 // Launch the power-table kernel of the handle's precision.
 int run_powers(polyeval *h, const pe::PowerParams &pp, cudaStream_t s) {
-  const cudaError_t e = h->wide ? pe::launch_powers_wide(pp, s) : pe::launch_powers(h->dd, pp, s);
+  const cudaError_t e = h->qd     ? pe::launch_powers_qd(pp, s)
+                        : h->wide ? pe::launch_powers_wide(pp, s)
+                                  : pe::launch_powers(h->dd, pp, s);
   if (e != cudaSuccess) return PE_ECUDA;
   if (pp.total > 0) h->kernels_launched++;
   return PE_OK;
@@ -172,7 +183,8 @@ Cost power_cost(bool dd, int emax) {
   return dd ? Cost{32 * m, 44 * m} : Cost{4 * m, 6 * m};
 }
 
-int validate(const pe_system *s, uint32_t flags) {
+// qd_coef: check the quad-double coefficients (coef_qd) instead of coef.
+int validate(const pe_system *s, uint32_t flags, bool qd_coef) {
   if (!s || !s->poly_ptr || !s->mono_ptr) return PE_EINVAL;
   if (s->n_vars < 1 || s->n_polys < 0) return PE_EINVAL;
   if (s->n_vars > PE_MAX_VARS) return PE_ERANGE;
@@ -187,7 +199,8 @@ int validate(const pe_system *s, uint32_t flags) {
   const int64_t nnz = s->mono_ptr[M];
   if (nnz > INT32_MAX - 1) return PE_ERANGE;
   if (nnz > 0 && (!s->pos || !s->exp)) return PE_EINVAL;
-  if (M > 0 && !s->coef) return PE_EINVAL;
+  if (M > 0 && !(qd_coef ? static_cast<const void *>(s->coef_qd) : static_cast<const void *>(s->coef)))
+    return PE_EINVAL;
   for (int64_t t = 0; t < M; t++) {
     for (int64_t j = s->mono_ptr[t]; j < s->mono_ptr[t + 1]; j++) {
       if (s->pos[j] < 0 || s->pos[j] >= s->n_vars) return PE_EINVAL;
@@ -195,10 +208,13 @@ int validate(const pe_system *s, uint32_t flags) {
       if (s->exp[j] < 1) return PE_EINVAL;
       if (s->exp[j] > PE_MAX_EXP) return PE_ERANGE;
     }
-    const pe_cdd &c = s->coef[t];
-    if (!std::isfinite(c.re_hi) || !std::isfinite(c.re_lo) || !std::isfinite(c.im_hi) || !std::isfinite(c.im_lo))
-      return PE_EINVAL;
-    const bool zero = c.re_hi == 0.0 && c.re_lo == 0.0 && c.im_hi == 0.0 && c.im_lo == 0.0;
+    const double *c = qd_coef ? &s->coef_qd[t].re[0] : &s->coef[t].re_hi;
+    const int nd = qd_coef ? 8 : 4;
+    bool zero = true;
+    for (int i = 0; i < nd; i++) {
+      if (!std::isfinite(c[i])) return PE_EINVAL;
+      zero = zero && c[i] == 0.0;
+    }
     if (zero && !(flags & PE_ALLOW_ZERO_COEF)) return PE_EINVAL;
   }
   return PE_OK;
@@ -212,12 +228,14 @@ struct Compiled {
   int32_t kmax = 0;
 };
 
-int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, bool wide, SysDesc &d) {
+int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, bool wide, bool qd, SysDesc &d) {
   d.n = s->n_vars;
   d.N = s->n_polys;
   d.poly0 = static_cast<int32_t>(c.poly_sys.size());
   int32_t emax = 1;
-  const Cost rc = row_cost(dd, s->n_vars);
+  // PE_QD_INT executes no FP64 arithmetic; its polynomials are ordered by the
+  // double-double cost, which grows with the same products and sums
+  const Cost rc = row_cost(dd || qd, s->n_vars);
   for (int32_t p = 0; p < s->n_polys; p++) {
     Cost pc = rc;
     for (int64_t t = s->poly_ptr[p]; t < s->poly_ptr[p + 1]; t++) {
@@ -231,11 +249,23 @@ int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, b
       }
       const int k = static_cast<int>(e - b);
       c.kmax = std::max(c.kmax, k);
-      const Cost mc = wide ? monomial_cost_wide(k) : monomial_cost(dd, k, n2);
+      const Cost mc = wide ? monomial_cost_wide(k) : monomial_cost(dd || qd, k, n2);
       pc.ops += mc.ops;
       pc.flops += mc.flops;
       if (c.var.size() > static_cast<size_t>(INT32_MAX - 1)) return PE_ERANGE;
       c.mono_ptr.push_back(static_cast<int32_t>(c.var.size()));
+      if (qd) {
+        // quad-double as given (the conversion kernel accepts any four
+        // doubles per part), else the double-double widened with zeros
+        if (s->coef_qd) {
+          const pe_cqd &q = s->coef_qd[t];
+          c.coef.insert(c.coef.end(), {q.re[0], q.re[1], q.re[2], q.re[3], q.im[0], q.im[1], q.im[2], q.im[3]});
+        } else {
+          const pe_cdd &q = s->coef[t];
+          c.coef.insert(c.coef.end(), {q.re_hi, q.re_lo, 0.0, 0.0, q.im_hi, q.im_lo, 0.0, 0.0});
+        }
+        continue;
+      }
       const pe_cdd &cf = s->coef[t];
       if (dd || wide) {
         // renormalised (FastTwoSum after ordering), so the first product of a
@@ -266,7 +296,7 @@ int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, b
 int finish_handle(polyeval *h, Compiled &c) {
   h->kmax = c.kmax;
   h->kslots = std::max(c.kmax - 1, 1);
-  if (h->wide && h->kslots > kWideSlotsFull) {
+  if ((h->wide && h->kslots > kWideSlotsFull) || (h->qd && h->kslots > kQdSlotsFull)) {
     // keep every second forward product (the others are recomputed in the
     // backward pass) so that enough warps fit in shared memory
     h->slot_stride = 2;
@@ -277,14 +307,18 @@ int finish_handle(polyeval *h, Compiled &c) {
   if (cudaGetDevice(&dev) != cudaSuccess) return PE_ECUDA;
   if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PE_ECUDA;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return PE_ECUDA;
-  const size_t per_warp =
-      static_cast<size_t>(h->kslots) * 32 * (h->wide ? pe::kWideSlotBytes : (h->dd ? 16 : 8));
+  const size_t per_warp = static_cast<size_t>(h->kslots) * 32 *
+                         (h->qd ? pe::kQdSlotBytes : h->wide ? pe::kWideSlotBytes : (h->dd ? 16 : 8));
   h->warps_per_block = pe::kWarpsPerBlockMax;
   while (h->warps_per_block > 1 && per_warp * h->warps_per_block > static_cast<size_t>(optin)) h->warps_per_block /= 2;
   if (per_warp * h->warps_per_block > static_cast<size_t>(optin)) return PE_ERANGE;
   h->smem_bytes = per_warp * h->warps_per_block;
   h->smem_per_warp = per_warp;
-  if (h->wide) {
+  if (h->qd) {
+    if (pe::prepare_main_qd(static_cast<size_t>(optin)) != cudaSuccess) return PE_ECUDA;
+    if (pe::main_qd_occupancy(h->warps_per_block, h->smem_bytes, &h->blocks_per_sm) != cudaSuccess) return PE_ECUDA;
+    if (pe::main_qd_occupancy(1, per_warp, &h->blocks_per_sm_1) != cudaSuccess) return PE_ECUDA;
+  } else if (h->wide) {
     if (pe::prepare_main_wide(static_cast<size_t>(optin)) != cudaSuccess) return PE_ECUDA;
     if (pe::main_wide_occupancy(h->warps_per_block, h->smem_bytes, &h->blocks_per_sm) != cudaSuccess) return PE_ECUDA;
     if (pe::main_wide_occupancy(1, per_warp, &h->blocks_per_sm_1) != cudaSuccess) return PE_ECUDA;
@@ -301,13 +335,16 @@ int finish_handle(polyeval *h, Compiled &c) {
     return rc;
   if ((rc = h->counter.alloc(sizeof(unsigned))) || (rc = h->status.alloc(sizeof(int)))) return rc;
   if (cudaMemset(h->status.p, 0, sizeof(int)) != cudaSuccess) return PE_ECUDA;
-  if (h->wide) {  // coefficients to the block format, once
-    const int64_t M = static_cast<int64_t>(c.coef.size() / 4);
-    if ((rc = h->coef_wide.alloc(static_cast<size_t>(M) * pe::kWideBytes)) != PE_OK) return rc;
-    if (pe::convert_coef_wide(static_cast<const double *>(h->coef.p), static_cast<uint32_t *>(h->coef_wide.p), M,
-                              nullptr) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess)
-      return PE_ECUDA;
+  if (block_format(h)) {  // coefficients to the block format, once
+    const int64_t M = static_cast<int64_t>(c.coef.size() / (h->qd ? 8 : 4));
+    if ((rc = h->coef_wide.alloc(static_cast<size_t>(M) * (h->qd ? pe::kQdBytes : pe::kWideBytes))) != PE_OK)
+      return rc;
+    const cudaError_t ce =
+        h->qd ? pe::convert_coef_qd(static_cast<const double *>(h->coef.p), static_cast<uint32_t *>(h->coef_wide.p), M,
+                                    nullptr)
+              : pe::convert_coef_wide(static_cast<const double *>(h->coef.p), static_cast<uint32_t *>(h->coef_wide.p),
+                                      M, nullptr);
+    if (ce != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return PE_ECUDA;
     h->coef.alloc(0);
   }
   return PE_OK;
@@ -344,7 +381,7 @@ void dd_times_int(double hi, double lo, double k, double &rh, double &rl) {
 // monomials in S_m order, the coefficients c a_j of the derivatives, then the
 // coefficients c themselves (Section 3.3).
 int setup_paper(polyeval *h, const pe_system *sys, const Compiled &c) {
-  if (!h->dd || h->wide) return PE_EINVAL;
+  if (!h->dd || h->wide || h->qd) return PE_EINVAL;
   const SysDesc &d = h->sys[0];
   if (d.N < 1 || h->max_points > 65535) return PE_EINVAL;
   const int64_t M = sys->poly_ptr[d.N];
@@ -401,7 +438,7 @@ pe::MainParams main_params(const polyeval *h) {
   p.poly_ptr = static_cast<const int32_t *>(h->poly_ptr.p);
   p.mono_ptr = static_cast<const int32_t *>(h->mono_ptr.p);
   p.var = static_cast<const uint32_t *>(h->var.p);
-  p.coef = static_cast<const double *>(h->wide ? h->coef_wide.p : h->coef.p);
+  p.coef = static_cast<const double *>(block_format(h) ? h->coef_wide.p : h->coef.p);
   p.poly_sys = static_cast<const int32_t *>(h->poly_sys.p);
   p.sys = static_cast<const SysDesc *>(h->sysd.p);
   p.perm = static_cast<const int32_t *>(h->perm.p);
@@ -430,8 +467,9 @@ int run_main(polyeval *h, const pe::MainParams &mp, cudaStream_t s, int mode = 0
   }
   if (e0 && cudaEventRecord(e0, s) != cudaSuccess) return PE_ECUDA;
   const Shape sh = shape_for(h, mp.n_items, mode);
-  const cudaError_t le = h->wide ? pe::launch_main_wide(mp, sh.warps, sh.smem, sh.grid, s)
-                                 : pe::launch_main(h->dd, mp, sh.warps, sh.smem, sh.grid, s);
+  const cudaError_t le = h->qd     ? pe::launch_main_qd(mp, sh.warps, sh.smem, sh.grid, s)
+                         : h->wide ? pe::launch_main_wide(mp, sh.warps, sh.smem, sh.grid, s)
+                                   : pe::launch_main(h->dd, mp, sh.warps, sh.smem, sh.grid, s);
   if (le != cudaSuccess) return PE_ECUDA;
   h->kernels_launched++;
   if (e1 && cudaEventRecord(e1, s) != cudaSuccess) return PE_ECUDA;
@@ -442,26 +480,46 @@ int run_main(polyeval *h, const pe::MainParams &mp, cudaStream_t s, int mode = 0
 
 extern "C" {
 
-int polyeval_validate(const pe_system *sys, uint32_t flags) { return validate(sys, flags); }
+int polyeval_validate(const pe_system *sys, uint32_t flags) {
+  return validate(sys, flags, sys && !sys->coef && sys->coef_qd);
+}
+
+}  // extern "C"
+
+namespace {
+
+bool valid_precision(int precision) {
+  return precision == PE_DD || precision == PE_F64 || precision == PE_DD_INT || precision == PE_QD_INT;
+}
+
+void set_precision(polyeval *h, int precision) {
+  h->dd = precision != PE_F64;
+  h->wide = precision == PE_DD_INT;
+  h->qd = precision == PE_QD_INT;
+}
+
+}  // namespace
+
+extern "C" {
+
 
 int polyeval_create(const pe_system *sys, int precision, uint32_t flags, int64_t max_points, polyeval_t **out) {
   if (!out) return PE_EINVAL;
   *out = nullptr;
-  if (precision != PE_DD && precision != PE_F64 && precision != PE_DD_INT) return PE_EINVAL;
+  if (!valid_precision(precision)) return PE_EINVAL;
   if (max_points < 1) return PE_EINVAL;
-  int rc = validate(sys, flags);
+  int rc = validate(sys, flags, sys && precision == PE_QD_INT && sys->coef_qd);
   if (rc != PE_OK) return rc;
   polyeval *h = nullptr;
   try {
     h = new polyeval();
-    h->dd = precision != PE_F64;
-    h->wide = precision == PE_DD_INT;
+    set_precision(h, precision);
     h->batch = false;
     h->count = 1;
     h->max_points = max_points;
     h->sys.resize(1);
     Compiled c;
-    if ((rc = append_system(c, sys, 0, h->dd, h->wide, h->sys[0])) != PE_OK) {
+    if ((rc = append_system(c, sys, 0, h->dd, h->wide, h->qd, h->sys[0])) != PE_OK) {
       delete h;
       return rc;
     }
@@ -483,9 +541,9 @@ int polyeval_create(const pe_system *sys, int precision, uint32_t flags, int64_t
       ops += c.poly_ops[p];
       flops += c.poly_flops[p];
     }
-    const Cost pw = h->wide ? Cost{} : power_cost(h->dd, d.emax);
-    h->ops_per_point = ops + pw.ops * d.n;
-    h->flops_per_point = flops + pw.flops * d.n;
+    const Cost pw = block_format(h) ? Cost{} : power_cost(h->dd, d.emax);
+    h->ops_per_point = h->qd ? 0.0 : ops + pw.ops * d.n;
+    h->flops_per_point = h->qd ? 0.0 : flops + pw.flops * d.n;
     if ((rc = finish_handle(h, c)) != PE_OK || (rc = h->perm.upload(perm)) != PE_OK) {
       delete h;
       return rc;
@@ -525,9 +583,9 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
   if (!out) return PE_EINVAL;
   *out = nullptr;
   if (!systems || !points_per_system || count < 1) return PE_EINVAL;
-  if (precision != PE_DD && precision != PE_F64 && precision != PE_DD_INT) return PE_EINVAL;
+  if (!valid_precision(precision)) return PE_EINVAL;
   for (int32_t s = 0; s < count; s++) {
-    int rc = validate(&systems[s], flags);
+    int rc = validate(&systems[s], flags, precision == PE_QD_INT && systems[s].coef_qd);
     if (rc != PE_OK) return rc;
     if (points_per_system[s] < 0 || points_per_system[s] > INT32_MAX) return PE_EINVAL;
   }
@@ -535,8 +593,7 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
   int rc = PE_OK;
   try {
     h = new polyeval();
-    h->dd = precision != PE_F64;
-    h->wide = precision == PE_DD_INT;
+    set_precision(h, precision);
     h->batch = true;
     h->count = count;
     h->sys.resize(count);
@@ -551,7 +608,7 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
     double ops = 0, flops = 0;
     for (int32_t s = 0; s < count; s++) {
       SysDesc &d = h->sys[s];
-      if ((rc = append_system(c, &systems[s], s, h->dd, h->wide, d)) != PE_OK) {
+      if ((rc = append_system(c, &systems[s], s, h->dd, h->wide, h->qd, d)) != PE_OK) {
         delete h;
         return rc;
       }
@@ -568,7 +625,7 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
       const bool tab = table_levels(h, d.emax) > 0 && P > 0;
       to += tab ? table_levels(h, d.emax) * d.n * P : 0;
       prefix.push_back(prefix.back() + (tab ? static_cast<int64_t>(d.n) * P : 0));
-      const Cost pw = h->wide ? Cost{} : power_cost(h->dd, d.emax);
+      const Cost pw = block_format(h) ? Cost{} : power_cost(h->dd, d.emax);
       ops += pw.ops * d.n * P;
       flops += pw.flops * d.n * P;
       for (int32_t p = 0; p < d.N; p++) {
@@ -594,8 +651,10 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
     }
     h->n_items_batch = static_cast<int64_t>(items.size());
     h->power_total_batch = prefix.back();
-    h->ops_per_point = ops;
-    h->flops_per_point = flops;
+    h->f_total_batch = fo;
+    h->J_total_batch = jo;
+    h->ops_per_point = h->qd ? 0.0 : ops;
+    h->flops_per_point = h->qd ? 0.0 : flops;
     if ((rc = finish_handle(h, c)) != PE_OK || (rc = h->items.upload(it2)) != PE_OK ||
         (rc = h->prefix.upload(prefix)) != PE_OK ||
         (rc = h->table.alloc(static_cast<size_t>(to) * table_entry_bytes(h))) != PE_OK) {
@@ -716,7 +775,15 @@ int eval_single(polyeval *h, const void *points, int64_t P, void *out_f, void *o
   mp.scratch_J = C > 1 ? mp.scratch_f + static_cast<size_t>(C - 1) * f_doubles : nullptr;
   mp.n_items = base * C;
   int rc = run_main(h, mp, s, mode);
-  if (rc != PE_OK || C == 1) return rc;
+  if (rc != PE_OK) return rc;
+  if (h->qd) {  // add the chunks' accumulators, round to quad-double
+    if (base > 0 && pe::launch_finalize_qd(mp.out_f, mp.out_J, mp.scratch_f, mp.scratch_J, 2 * static_cast<int64_t>(d.N) * P,
+                                           2 * static_cast<int64_t>(d.N) * d.n * P, C, s) != cudaSuccess)
+      return PE_ECUDA;
+    if (base > 0) h->kernels_launched++;
+    return PE_OK;
+  }
+  if (C == 1) return rc;
   if (pe::launch_combine(h->dd, mp.out_f, mp.out_J, mp.scratch_f, mp.scratch_J, f_doubles, J_doubles, C, s) !=
       cudaSuccess)
     return PE_ECUDA;
@@ -796,7 +863,7 @@ int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void *out_f,
 
 
 int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, void *out_J, double *norms, void *stream) {
-  if (!h || h->batch) return PE_EINVAL;
+  if (!h || h->batch || h->qd) return PE_EINVAL;
   const SysDesc &d = h->sys[0];
   if (d.N != d.n) return PE_EINVAL;
   int rc = polyeval_eval(h, points, P, out_f, out_J, stream);
@@ -837,7 +904,13 @@ int polyeval_eval_many(polyeval_t *h, const void *points, void *out_f, void *out
   mp.single_T = 0;
   mp.n_chunks = 1;
   mp.n_items = h->n_items_batch;
-  return run_main(h, mp, s);
+  const int rc = run_main(h, mp, s);
+  if (rc != PE_OK || !h->qd) return rc;
+  if (pe::launch_finalize_qd(mp.out_f, mp.out_J, nullptr, nullptr, 2 * h->f_total_batch, 2 * h->J_total_batch, 1, s) !=
+      cudaSuccess)
+    return PE_ECUDA;
+  h->kernels_launched++;
+  return PE_OK;
 }
 
 int polyeval_eval_host(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream) {

@@ -31,7 +31,7 @@ struct MainParams {
   const int32_t *poly_ptr;  // [Ntot+1] global monomial offsets
   const int32_t *mono_ptr;  // [Mtot+1] offsets into var
   const uint32_t *var;      // [nnz] position | exponent << 16
-  const double *coef;       // [Mtot] complex coefficients (4 or 2 doubles)
+  const double *coef;       // [Mtot] complex coefficients (4 or 2 doubles; block format for the integer paths)
   const int32_t *poly_sys;  // [Ntot] system of each global polynomial
   const SysDesc *sys;       // [count]
   const int32_t *perm;      // single handle: polynomials by decreasing cost
@@ -119,5 +119,22 @@ cudaError_t launch_powers_wide(const PowerParams &p, cudaStream_t s);
 cudaError_t prepare_main_wide(size_t smem_bytes);
 cudaError_t main_wide_occupancy(int warps_per_block, size_t smem_bytes, int *blocks_per_sm);
 cudaError_t launch_main_wide(const MainParams &p, int warps_per_block, size_t smem_bytes, int grid, cudaStream_t s);
+
+// Quad-double evaluation on the integer pipes (kernels_qd.cu): 256-bit block
+// floating point products, 224-bit integer accumulators written in place into
+// the outputs, rounded to quad-double by launch_finalize_qd.  Table entries
+// and coefficients are 80 bytes.
+constexpr int kQdBytes = 80;
+constexpr int kQdSlotBytes = 9 * 4;  // per lane and prefix-product slot
+cudaError_t convert_coef_qd(const double *coef_qd, uint32_t *coef_blk, int64_t M, cudaStream_t s);
+cudaError_t launch_powers_qd(const PowerParams &p, cudaStream_t s);
+cudaError_t prepare_main_qd(size_t smem_bytes);
+cudaError_t main_qd_occupancy(int warps_per_block, size_t smem_bytes, int *blocks_per_sm);
+cudaError_t launch_main_qd(const MainParams &p, int warps_per_block, size_t smem_bytes, int grid, cudaStream_t s);
+// Sums the accumulators of `chunks` copies (the outputs, then scratch copies
+// 1 .. chunks-1 of the same layout) and rounds them to quad-double in the
+// outputs.  Components are 32-byte halves of a complex entry.
+cudaError_t launch_finalize_qd(double *out_f, double *out_J, const double *scratch_f, const double *scratch_J,
+                               int64_t f_components, int64_t J_components, int chunks, cudaStream_t s);
 
 }  // namespace pe

@@ -19,10 +19,11 @@ Arrays (CSR by polynomial, then by monomial):
                              inside a monomial
 * ``exp``       int32 [nnz]  exponent >= 1
 * ``coef``      float64 [M, 4]  complex double-double (re_hi, re_lo,
-                                im_hi, im_lo)
+                                im_hi, im_lo), or [M, 8] complex
+                                quad-double (re0..re3, im0..im3)
 
 Points are float64 [n, P, 4]: structure of arrays, variable-major, each entry
-a complex double-double.
+a complex double-double ([n, P, 8] for quad-double points).
 
 Every random draw goes through numpy's PCG64 and only IEEE basic operations
 (+, -, *, /, exact scaling by powers of two), so the same seed gives the same
@@ -63,11 +64,21 @@ class System:
         return self.pos[a:b].tolist(), self.exp[a:b].tolist()
 
     def as_fp64(self) -> "System":
-        """Same system with the low words of the coefficients set to zero."""
-        c = self.coef.copy()
-        c[:, 1] = 0.0
-        c[:, 3] = 0.0
+        """Same system with every coefficient part but the leading one of
+        each component set to zero."""
+        w = self.coef.shape[1] // 2
+        c = np.zeros_like(self.coef)
+        c[:, 0] = self.coef[:, 0]
+        c[:, w] = self.coef[:, w]
         return System(self.n_vars, self.n_polys, self.poly_ptr, self.mono_ptr, self.pos, self.exp, c, dict(self.meta))
+
+    def to_qd(self, seed: int) -> "System":
+        """Same monomials, coefficients widened to quad-double: the
+        double-double parts kept and two random lower parts added
+        (``widen_qd``)."""
+        rng = np.random.Generator(np.random.PCG64(seed))
+        return System(self.n_vars, self.n_polys, self.poly_ptr, self.mono_ptr, self.pos, self.exp,
+                      widen_qd(rng, self.coef), dict(self.meta))
 
 
 # ----------------------------------------------------------------------------
@@ -121,6 +132,21 @@ def random_cdd(rng, size, modulus=None):
     out[:, 1] = _low_words(rng, re)
     out[:, 2] = im
     out[:, 3] = _low_words(rng, im)
+    return out
+
+
+def widen_qd(rng, cdd):
+    """Complex double-doubles [..., 4] to complex quad-doubles [..., 8]: the
+    two parts of each component kept, then two random lower parts, each below
+    a quarter unit in the last place of the part before it (so the result is
+    a normalised quad-double when the input is a normalised double-double)."""
+    cdd = np.asarray(cdd, dtype=np.float64)
+    out = np.empty(cdd.shape[:-1] + (8,), dtype=np.float64)
+    for c in range(2):
+        out[..., 4 * c] = cdd[..., 2 * c]
+        out[..., 4 * c + 1] = cdd[..., 2 * c + 1]
+        out[..., 4 * c + 2] = _low_words(rng, out[..., 4 * c + 1])
+        out[..., 4 * c + 3] = _low_words(rng, out[..., 4 * c + 2])
     return out
 
 

@@ -11,6 +11,10 @@ import numpy as np
 
 DD_TOL = 1e-28
 F64_TOL = 1e-13
+# quad-double: products err by about 2^-246, each sum by 2^-219 of its largest
+# term, the final rounding by 2^-211 of the value; 1e-60 leaves a factor of
+# several hundred over that bound (and is 1e32 times tighter than DD_TOL)
+QD_TOL = 1e-60
 
 # the precisions of the library: double-double, double, double-double with
 # integer-pipe products
@@ -18,13 +22,13 @@ PRECS = ["dd", "f64", "ddint"]
 
 
 def tol(prec):
-    return F64_TOL if prec == "f64" else DD_TOL
+    return F64_TOL if prec == "f64" else QD_TOL if prec == "qd" else DD_TOL
 
 
 def pe_precision(prec):
     import paper_1201_0499_gb300 as pkg
 
-    return {"dd": pkg.PE_DD, "f64": pkg.PE_F64, "ddint": pkg.PE_DD_INT}[prec]
+    return {"dd": pkg.PE_DD, "f64": pkg.PE_F64, "ddint": pkg.PE_DD_INT, "qd": pkg.PE_QD_INT}[prec]
 
 
 def widen(x2):
@@ -90,10 +94,10 @@ def scales(system, pts):
     k = np.diff(system.mono_ptr).astype(np.int64)
     kmax = int(k.max()) if k.size else 0
     poly_of = np.repeat(np.arange(N), np.diff(system.poly_ptr))
-    ac = np.hypot(system.coef[:, 0], system.coef[:, 2])
+    ac = np.hypot(system.coef[:, 0], system.coef[:, system.coef.shape[1] // 2])
     rows = np.repeat(np.arange(M), k)
     cols = np.arange(system.pos.size) - np.repeat(system.mono_ptr[:-1], k)
-    ax_all = np.hypot(pts[..., 0], pts[..., 2])  # [n, P]
+    ax_all = np.hypot(pts[..., 0], pts[..., pts.shape[-1] // 2])  # [n, P]
     for q in range(P):
         ax = ax_all[:, q]
         W = np.ones((M, max(kmax, 1)))
@@ -110,9 +114,11 @@ def scales(system, pts):
 
 
 def dd_diff(a, b):
-    """|a - b| for complex double-double arrays [..., 4], in float64."""
-    re = (a[..., 0] - b[..., 0]) + (a[..., 1] - b[..., 1])
-    im = (a[..., 2] - b[..., 2]) + (a[..., 3] - b[..., 3])
+    """|a - b| for complex multi-double arrays [..., 4] or [..., 8] (the
+    parts of each component subtracted pairwise), in float64."""
+    w = a.shape[-1] // 2
+    re = sum(a[..., i] - b[..., i] for i in range(w))
+    im = sum(a[..., w + i] - b[..., w + i] for i in range(w))
     return np.hypot(re, im)
 
 

@@ -9,6 +9,9 @@ Section 2, Eq. (1) that ``oracle.exact`` writes out:
   index mistakes) and whose value is a numpy matrix-vector product;
 * Euler's identity sum_i x_i df/dx_i = d f on homogeneous systems;
 * closed forms: c x^a and the Speelpenning product x_1 ... x_k;
+* quad-double data: the dual-number route again with every coefficient and
+  point a sum of four doubles whose lower two parts lie below double-double
+  precision;
 * brute force over all small monomials with Gaussian-integer data, the value
   from numpy and each derivative by exact Lagrange interpolation along the
   variable's line;
@@ -33,7 +36,11 @@ from oracle import exact as E
 # ----------------------------------------------------------------------------
 
 def fr_from_dd(v):
-    return (Fraction(v[0]) + Fraction(v[1]), Fraction(v[2]) + Fraction(v[3]))
+    """A complex multi-double (2, 4 or 8 doubles: real parts, then imaginary
+    parts) as a pair of Fractions."""
+    w = len(v) // 2
+    return (sum((Fraction(float(x)) for x in v[:w]), Fraction(0)),
+            sum((Fraction(float(x)) for x in v[w:2 * w]), Fraction(0)))
 
 
 def fr_from_exact(z):
@@ -279,7 +286,26 @@ def check_brute_force(seed=5):
     return True
 
 
-CHECKS = [check_dual, check_linear, check_euler, check_closed_forms, check_brute_force]
+def check_quad_double(seed=6):
+    """Dual numbers over quad-double coefficients and points."""
+    s = random_dd_system(seed, n=4, N=3, m=5, kmax=3, emax=3).to_qd(seed + 1)
+    rng = np.random.Generator(np.random.PCG64(seed + 2))
+    pts = synth.widen_qd(rng, synth.points(seed + 7, 4, 2))
+    # the lower parts matter: dropping them changes the data
+    assert any(fr_from_dd(c) != fr_from_dd(c[[0, 1, 4, 5]]) for c in s.coef)
+    for q in range(2):
+        f, J = E.evaluate_point(s, pts, q)
+        for i in range(s.n_vars):
+            ref = dual_eval(s, pts, q, i)
+            for p in range(s.n_polys):
+                if fr_from_exact(f[p]) != ref[p][0]:
+                    return False
+                if fr_from_exact(J[p].get(i, E.ZERO)) != ref[p][1]:
+                    return False
+    return True
+
+
+CHECKS = [check_dual, check_linear, check_euler, check_closed_forms, check_brute_force, check_quad_double]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=lambda c: c.__name__)
@@ -331,7 +357,17 @@ def _mut_index(self, t):
     return pos, exp
 
 
+_orig_from_dd = E.cx_from_dd
+
+
+def _mut_two_parts(v):
+    """Reads only the leading two parts of each component."""
+    w = len(v) // 2
+    return _orig_from_dd([v[0], v[1], v[w], v[w + 1]])
+
+
 MUTATIONS = {
+    "quad_double_low_parts_dropped": (E, "cx_from_dd", _mut_two_parts),
     "wrong_sign": (E, "cx_mul", _mut_sign),
     "dropped_exponent_factor": (E, "cx_scale", _mut_scale),
     "power_off_by_one": (E, "powers_of", _mut_powers),
