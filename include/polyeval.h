@@ -342,6 +342,92 @@ PE_API int polyeval_status(polyeval_t *h);
 PE_API int polyeval_eval_noalloc(const pe_system *dev_sys, int32_t max_k, int32_t max_exp, const void *points,
                                  int64_t P, void *out_f, void *out_J, void *stream);
 
+/* ---- path tracking ------------------------------------------------------
+ *
+ * Solving F(x) = 0 (a square system, n_polys == n_vars) by homotopy
+ * continuation, the application the paper's evaluation serves (Section 1:
+ * evaluation inside Newton's method, the corrector of a path tracker; only a
+ * few paths need double-double).  The homotopy is
+ *     H(x, t) = gamma (1 - t) G(x) + t F(x),   G_i(x) = x_i^(d_i) - 1,
+ * with d_i the total degree of polynomial i and gamma a complex constant
+ * (for generic gamma every path is regular on [0, 1)).  The start solutions
+ * are the prod d_i points whose coordinates are roots of unity.  Every path
+ * is one point of the evaluator's batch; one iteration evaluates F and J_F
+ * at all points (polyeval_eval) and then advances each path by one step of
+ * its own state machine (one warp per path): Newton corrector at t1
+ * (accepted when max|dx| <= corr_tol max(1, max|x|) within max_corr steps
+ * that keep shrinking, else rejected: back to the last accepted point, step
+ * size halved, failed below h_min), Euler predictor along the tangent
+ * (H_x v = -H_t, t1 = min(t + h, 1)), step size doubled after succ_grow
+ * accepted steps in a row (at most h_max), and at t = 1 Newton's method on
+ * F until max|dx| <= end_tol max(1, max|x|) (at most max_end steps).
+ */
+typedef struct {
+  double gamma_re, gamma_im; /* gamma (nonzero)                                   */
+  double h_init, h_min, h_max; /* step sizes in t                                   */
+  double corr_tol, end_tol;  /* relative step tolerances (see above)              */
+  double x_big;              /* max|x| above which a path counts as diverging     */
+  int32_t max_corr, max_end, succ_grow;
+  int64_t max_iters;         /* iterations (evaluations) of the whole batch, at most */
+} pe_track_params;
+
+/* Status of a path after polyeval_track / polyeval_track_adaptive. */
+#define PE_PATH_RUNNING 0       /* max_iters reached first                         */
+#define PE_PATH_SUCCESS 1       /* reached t = 1 and converged there               */
+#define PE_PATH_FAILED 2        /* step size fell below h_min                      */
+#define PE_PATH_DIVERGED 3      /* max|x| exceeded x_big                           */
+#define PE_PATH_END_NOT_CONVERGED 4 /* at t = 1 Newton did not reach end_tol (singular or ill-conditioned end point) */
+
+/* Default tracking parameters for a precision (PE_DD, PE_DD_INT or PE_F64). */
+PE_API int polyeval_track_defaults(int precision, pe_track_params *prm);
+
+/* The Bezout number prod d_i (the number of paths) as a double, and the
+ * degrees d_i into degrees[n] (either may be NULL).  Single-system handles. */
+PE_API int polyeval_bezout(const polyeval_t *h, double *count, int32_t *degrees);
+
+/*
+ * Start solutions of G(x) = 0 for paths first .. first + P - 1 into the
+ * device array points [n][P] (pe_cdd or pe_c64 as the handle's precision):
+ * path r has coordinates x_i = exp(2 pi i k_i / d_i) with k_i the mixed-radix
+ * digits of r (radices d_0, d_1, ...).  Asynchronous on stream.  Errors:
+ * PE_EINVAL for a handle that cannot track (batch, PE_QD_INT, paper
+ * kernels, not square, a polynomial of degree 0) or bad arguments.
+ */
+PE_API int polyeval_start_points(polyeval_t *h, int64_t first, int64_t P, void *points, void *stream);
+
+/*
+ * Track P paths from the start points in `points` (device [n][P], the
+ * handle's precision; on return the end points) from t = 0 to t = 1.
+ *   t, status   device [P] arrays (either may be NULL): the last accepted t
+ *               and the PE_PATH_* status of each path
+ *   iterations  host, or NULL: iterations the batch took
+ * Blocks the calling thread: it synchronises `stream` every 8 iterations to
+ * read how many paths still run, and returns when none does (or after
+ * max_iters).  Allocates the tracker's scratch on the handle on first use
+ * (F, J_F, saved points, path states for P paths).  Not for stream capture.
+ * Errors: PE_EINVAL (as polyeval_start_points, bad parameters), PE_ERANGE
+ * (P > max_points), PE_ENOMEM, PE_ECUDA.
+ */
+PE_API int polyeval_track(polyeval_t *h, const pe_track_params *prm, void *points, int64_t P, double *t,
+                          int32_t *status, int64_t *iterations, void *stream);
+
+/*
+ * Adaptive precision: every path is tracked in double (h_lo, a PE_F64 handle
+ * of the system); the end points of the paths that succeed are refined by
+ * three Newton steps in double-double (h_hi, a PE_DD or PE_DD_INT handle of
+ * the same system), and only the paths that did not succeed are tracked
+ * again, from their start points, in double-double.
+ *   points     device [n][P] pe_cdd: start points in, end points out
+ *   status     device [P]: PE_PATH_* of each path (of its final tracking)
+ *   escalated  host, or NULL: the number of paths tracked in double-double
+ * Blocks like polyeval_track.  Errors: PE_EINVAL (wrong precisions, systems
+ * of different shape or degrees, bad parameters), PE_ERANGE, PE_ENOMEM,
+ * PE_ECUDA.
+ */
+PE_API int polyeval_track_adaptive(polyeval_t *h_lo, polyeval_t *h_hi, const pe_track_params *prm_lo,
+                                   const pe_track_params *prm_hi, void *points, int64_t P, int32_t *status,
+                                   int64_t *escalated, void *stream);
+
 /* Free a handle and its device memory (NULL is accepted). */
 PE_API void polyeval_destroy(polyeval_t *h);
 

@@ -36,6 +36,12 @@ PE_PAPER_KERNELS = 2
 PE_MAX_VARS = 65535
 PE_MAX_EXP = 256
 
+PE_PATH_RUNNING = 0
+PE_PATH_SUCCESS = 1
+PE_PATH_FAILED = 2
+PE_PATH_DIVERGED = 3
+PE_PATH_END_NOT_CONVERGED = 4
+
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpolyeval.so")
 
 _lib = None
@@ -57,6 +63,23 @@ class pe_system(ctypes.Structure):
         ("exp", ctypes.c_void_p),
         ("coef", ctypes.c_void_p),
         ("coef_qd", ctypes.c_void_p),
+    ]
+
+
+class pe_track_params(ctypes.Structure):
+    _fields_ = [
+        ("gamma_re", ctypes.c_double),
+        ("gamma_im", ctypes.c_double),
+        ("h_init", ctypes.c_double),
+        ("h_min", ctypes.c_double),
+        ("h_max", ctypes.c_double),
+        ("corr_tol", ctypes.c_double),
+        ("end_tol", ctypes.c_double),
+        ("x_big", ctypes.c_double),
+        ("max_corr", ctypes.c_int32),
+        ("max_end", ctypes.c_int32),
+        ("succ_grow", ctypes.c_int32),
+        ("max_iters", ctypes.c_int64),
     ]
 
 
@@ -92,6 +115,12 @@ def load_library(path: Optional[str] = None):
         "polyeval_newton": ([P, P, I64, P, P, P, P], ctypes.c_int),
         "polyeval_autotune": ([P, P, I64, P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                               ctypes.c_int),
+        "polyeval_track_defaults": ([ctypes.c_int, ctypes.POINTER(pe_track_params)], ctypes.c_int),
+        "polyeval_bezout": ([P, D, ctypes.POINTER(I32)], ctypes.c_int),
+        "polyeval_start_points": ([P, I64, I64, P, P], ctypes.c_int),
+        "polyeval_track": ([P, ctypes.POINTER(pe_track_params), P, I64, P, P, ctypes.POINTER(I64), P], ctypes.c_int),
+        "polyeval_track_adaptive": ([P, P, ctypes.POINTER(pe_track_params), ctypes.POINTER(pe_track_params), P, I64,
+                                     P, ctypes.POINTER(I64), P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -272,6 +301,44 @@ def polyeval_eval_noalloc(dev_sys: pe_system, max_k: int, max_exp: int, points, 
            "polyeval_eval_noalloc")
 
 
+def polyeval_track_defaults(precision: int) -> pe_track_params:
+    prm = pe_track_params()
+    _check(load_library().polyeval_track_defaults(precision, ctypes.byref(prm)), "polyeval_track_defaults")
+    return prm
+
+
+def polyeval_bezout(h: int, n: int):
+    """(number of paths, [d_0, ..., d_{n-1}])."""
+    c = ctypes.c_double()
+    d = (ctypes.c_int32 * n)()
+    _check(load_library().polyeval_bezout(h, ctypes.byref(c), d), "polyeval_bezout")
+    return c.value, list(d)
+
+
+def polyeval_start_points(h: int, first: int, P: int, points, stream=None) -> None:
+    _check(load_library().polyeval_start_points(h, int(first), int(P), _addr(points), _stream(stream)),
+           "polyeval_start_points")
+
+
+def polyeval_track(h: int, prm: pe_track_params, points, P: int, t=None, status=None, stream=None) -> int:
+    """Track P paths in place; returns the number of iterations."""
+    it = ctypes.c_int64()
+    _check(load_library().polyeval_track(h, ctypes.byref(prm), _addr(points), int(P), _addr(t), _addr(status),
+                                         ctypes.byref(it), _stream(stream)), "polyeval_track")
+    return it.value
+
+
+def polyeval_track_adaptive(h_lo: int, h_hi: int, prm_lo: pe_track_params, prm_hi: pe_track_params, points, P: int,
+                            status, stream=None) -> int:
+    """Track in double, refine or re-track in double-double; returns the
+    number of paths tracked again in double-double."""
+    esc = ctypes.c_int64()
+    _check(load_library().polyeval_track_adaptive(h_lo, h_hi, ctypes.byref(prm_lo), ctypes.byref(prm_hi),
+                                                  _addr(points), int(P), _addr(status), ctypes.byref(esc),
+                                                  _stream(stream)), "polyeval_track_adaptive")
+    return esc.value
+
+
 # ----------------------------------------------------------------------------
 # convenience wrappers over torch device memory
 # ----------------------------------------------------------------------------
@@ -338,6 +405,30 @@ class PolyEval:
 
     def cost(self):
         return polyeval_cost(self.handle)
+
+    def bezout(self):
+        """(number of paths of the total-degree homotopy, degrees)."""
+        return polyeval_bezout(self.handle, self.n_vars)
+
+    def start_points(self, P: int, first: int = 0, device="cuda", stream=None):
+        """Start solutions of paths first .. first + P - 1 as a CUDA tensor [n, P, c]."""
+        import torch
+
+        x = torch.empty((self.n_vars, P, _elem(self.precision)), dtype=torch.float64, device=device)
+        polyeval_start_points(self.handle, first, P, x, stream)
+        return x
+
+    def track(self, points, prm: Optional[pe_track_params] = None, stream=None):
+        """Track the paths starting at ``points`` (updated in place to the end
+        points); returns (status [P] int32, t [P], iterations)."""
+        import torch
+
+        P = points.shape[1]
+        prm = prm or polyeval_track_defaults(self.precision)
+        status = torch.empty(P, dtype=torch.int32, device=points.device)
+        t = torch.empty(P, dtype=torch.float64, device=points.device)
+        it = polyeval_track(self.handle, prm, points, P, t, status, stream)
+        return status, t, it
 
     def status(self) -> int:
         return polyeval_status(self.handle)

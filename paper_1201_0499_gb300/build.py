@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libpolyeval.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["kernels.cu", "kernels_wide.cu", "kernels_qd.cu", "newton.cu", "three_kernel.cu", "host.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "kernels_wide.cu", "kernels_qd.cu", "newton.cu", "track.cu", "three_kernel.cu", "host.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,6 +1,6 @@
 // Complex numbers held whole by one thread (both parts), in double-double
 // (CDD) and in double (C64): the arithmetic of the one-thread-per-item
-// kernels (Newton solve, the paper's three-kernel evaluation).
+// kernels (Newton solve, path tracker, the paper's three-kernel evaluation).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,6 +26,15 @@ struct CDD {
     reinterpret_cast<double2 *>(p)[1] = make_double2(im.h, im.l);
   }
   __device__ static CDD zero() { return CDD{dd{0.0, 0.0}, dd{0.0, 0.0}}; }
+  __device__ static CDD make(double re, double im) { return CDD{dd{re, 0.0}, dd{im, 0.0}}; }
+  // x * k for a double k, renormalised
+  __device__ static CDD scale(const CDD &x, double k) {
+    return CDD{normalize(pe::scale(x.re, k)), normalize(pe::scale(x.im, k))};
+  }
+  __device__ static CDD sub(const CDD &a, const CDD &b) {
+    return CDD{normalize(add(a.re, negate_if(b.re, 0x8000000000000000ULL))),
+               normalize(add(a.im, negate_if(b.im, 0x8000000000000000ULL)))};
+  }
   __device__ double abs_hi() const { return sqrt(re.h * re.h + im.h * im.h); }
   __device__ CDD neg() const { return CDD{negate_if(re, 0x8000000000000000ULL), negate_if(im, 0x8000000000000000ULL)}; }
   // x * y, renormalised
@@ -63,6 +72,9 @@ struct C64 {
   }
   __device__ void store(double *p) const { reinterpret_cast<double2 *>(p)[0] = make_double2(re, im); }
   __device__ static C64 zero() { return C64{0.0, 0.0}; }
+  __device__ static C64 make(double re, double im) { return C64{re, im}; }
+  __device__ static C64 scale(const C64 &x, double k) { return C64{__dmul_rn(x.re, k), __dmul_rn(x.im, k)}; }
+  __device__ static C64 sub(const C64 &a, const C64 &b) { return C64{__dsub_rn(a.re, b.re), __dsub_rn(a.im, b.im)}; }
   __device__ double abs_hi() const { return sqrt(re * re + im * im); }
   __device__ C64 neg() const { return C64{-re, -im}; }
   __device__ static C64 mul(const C64 &x, const C64 &y) {

@@ -88,6 +88,10 @@ struct polyeval {
   DeviceBuf stage_pts, stage_f, stage_J;
   DeviceBuf scratch;  // chunk partial results (single-system handles)
   DeviceBuf paper_coeffs, paper_cf, paper_mons;  // three-kernel design
+  // path tracking (single square systems): degrees of the polynomials and
+  // the tracker's scratch, allocated on first use
+  std::vector<int32_t> degrees;
+  DeviceBuf deg_dev, tr_f, tr_J, tr_xs, tr_state, tr_active, tr_x64, tr_status, tr_xc, tr_statc, tr_idx;
   struct Tuned {
     int64_t P;
     int chunks;
@@ -222,6 +226,7 @@ int validate(const pe_system *s, uint32_t flags, bool qd_coef) {
 
 struct Compiled {
   std::vector<int32_t> poly_ptr{0}, mono_ptr{0}, poly_sys;
+  std::vector<int32_t> poly_deg;  // total degree of each polynomial
   std::vector<uint32_t> var;
   std::vector<double> coef;
   std::vector<double> poly_ops, poly_flops;  // per point, per global polynomial
@@ -238,15 +243,19 @@ int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, b
   const Cost rc = row_cost(dd || qd, s->n_vars);
   for (int32_t p = 0; p < s->n_polys; p++) {
     Cost pc = rc;
+    int32_t pdeg = 0;
     for (int64_t t = s->poly_ptr[p]; t < s->poly_ptr[p + 1]; t++) {
       const int64_t b = s->mono_ptr[t], e = s->mono_ptr[t + 1];
       int n2 = 0;
+      int32_t mdeg = 0;
       for (int64_t j = b; j < e; j++) {
         const uint32_t a = static_cast<uint32_t>(s->exp[j]);
         c.var.push_back(static_cast<uint32_t>(s->pos[j]) | (a << 16));
         if (a >= 2) n2++;
+        mdeg += static_cast<int32_t>(a);
         emax = std::max<int32_t>(emax, static_cast<int32_t>(a));
       }
+      pdeg = std::max(pdeg, mdeg);
       const int k = static_cast<int>(e - b);
       c.kmax = std::max(c.kmax, k);
       const Cost mc = wide ? monomial_cost_wide(k) : monomial_cost(dd || qd, k, n2);
@@ -286,6 +295,7 @@ int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, b
     if (c.mono_ptr.size() > static_cast<size_t>(INT32_MAX - 1)) return PE_ERANGE;
     c.poly_ptr.push_back(static_cast<int32_t>(c.mono_ptr.size() - 1));
     c.poly_sys.push_back(sys_index);
+    c.poly_deg.push_back(pdeg);
     c.poly_ops.push_back(pc.ops);
     c.poly_flops.push_back(pc.flops);
   }
@@ -548,6 +558,7 @@ int polyeval_create(const pe_system *sys, int precision, uint32_t flags, int64_t
       delete h;
       return rc;
     }
+    h->degrees = c.poly_deg;
     if (flags & PE_PAPER_KERNELS) {
       if ((rc = setup_paper(h, sys, c)) != PE_OK) {
         delete h;
@@ -999,6 +1010,220 @@ const char *polyeval_strerror(int code) {
 int polyeval_fp64_peak(void *stream, double *fma_per_s, double *sm_clock_mhz) {
   return pe::fp64_peak_probe(static_cast<cudaStream_t>(stream), fma_per_s, sm_clock_mhz) == cudaSuccess ? PE_OK
                                                                                                         : PE_ECUDA;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// path tracking
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// A handle the tracker accepts: one square system in double-double or double
+// whose polynomials all have degree >= 1.
+bool trackable(const polyeval *h) {
+  if (!h || h->batch || h->qd || h->paper) return false;
+  const SysDesc &d = h->sys[0];
+  if (d.N != d.n || d.n < 1 || static_cast<int32_t>(h->degrees.size()) != d.n) return false;
+  for (int32_t g : h->degrees)
+    if (g < 1) return false;
+  return true;
+}
+
+int ensure(DeviceBuf &b, size_t bytes) { return b.bytes >= bytes ? PE_OK : b.alloc(bytes); }
+
+int upload_degrees(polyeval *h) {
+  if (h->deg_dev.p) return PE_OK;
+  return h->deg_dev.upload(h->degrees);
+}
+
+// Scratch for tracking P paths on handle h: F, J_F, the accepted points, the
+// path states and the running-path counter.
+int track_scratch(polyeval *h, int64_t P) {
+  const SysDesc &d = h->sys[0];
+  const size_t eb = static_cast<size_t>(elem_doubles(h)) * sizeof(double);
+  const size_t np = static_cast<size_t>(d.n) * static_cast<size_t>(P);
+  int rc;
+  if ((rc = upload_degrees(h)) || (rc = ensure(h->tr_f, eb * np)) || (rc = ensure(h->tr_J, eb * np * d.n)) ||
+      (rc = ensure(h->tr_xs, eb * np)) || (rc = ensure(h->tr_state, sizeof(pe::TrackState) * static_cast<size_t>(P))) ||
+      (rc = ensure(h->tr_active, sizeof(unsigned))))
+    return rc;
+  return PE_OK;
+}
+
+bool params_ok(const pe_track_params *p) {
+  return p && p->h_init > 0.0 && p->h_min > 0.0 && p->h_max >= p->h_init && p->h_init >= p->h_min &&
+         p->corr_tol > 0.0 && p->end_tol > 0.0 && p->x_big > 0.0 && p->max_corr >= 1 && p->max_end >= 1 &&
+         p->succ_grow >= 1 && p->max_iters >= 1 && std::isfinite(p->gamma_re) && std::isfinite(p->gamma_im) &&
+         (p->gamma_re != 0.0 || p->gamma_im != 0.0);
+}
+
+int track(polyeval *h, const pe_track_params *prm, double *x, int64_t P, double *t_out, int32_t *status,
+          int64_t *iterations, cudaStream_t s) {
+  if (iterations) *iterations = 0;
+  if (P == 0) return PE_OK;
+  int rc = track_scratch(h, P);
+  if (rc != PE_OK) return rc;
+  const SysDesc &d = h->sys[0];
+  pe::TrackParams tp{};
+  tp.n = d.n;
+  tp.P = P;
+  tp.J = static_cast<double *>(h->tr_J.p);
+  tp.f = static_cast<double *>(h->tr_f.p);
+  tp.x = x;
+  tp.xs = static_cast<double *>(h->tr_xs.p);
+  tp.st = static_cast<pe::TrackState *>(h->tr_state.p);
+  tp.deg = static_cast<const int32_t *>(h->deg_dev.p);
+  tp.gre = prm->gamma_re;
+  tp.gim = prm->gamma_im;
+  tp.h_min = prm->h_min;
+  tp.h_max = prm->h_max;
+  tp.corr_tol = prm->corr_tol;
+  tp.end_tol = prm->end_tol;
+  tp.x_big = prm->x_big;
+  tp.max_corr = prm->max_corr;
+  tp.max_end = prm->max_end;
+  tp.succ_grow = prm->succ_grow;
+  tp.active = static_cast<unsigned *>(h->tr_active.p);
+  if (pe::launch_track_init(h->dd, tp, prm->h_init, s) != cudaSuccess) return PE_ECUDA;
+  int64_t it = 0;
+  unsigned running = 1;
+  while (it < prm->max_iters && running) {
+    if (cudaMemsetAsync(tp.active, 0, sizeof(unsigned), s) != cudaSuccess) return PE_ECUDA;
+    if ((rc = polyeval_eval(h, x, P, tp.f, tp.J, s)) != PE_OK) return rc;
+    if (pe::launch_track_step(h->dd, tp, s) != cudaSuccess) return PE_ECUDA;
+    h->kernels_launched++;
+    it++;
+    if ((it & 7) == 0 || it == prm->max_iters) {
+      if (cudaMemcpyAsync(&running, tp.active, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return PE_ECUDA;
+    }
+  }
+  if (pe::launch_track_finish(tp.st, P, t_out, status, s) != cudaSuccess) return PE_ECUDA;
+  if (iterations) *iterations = it;
+  return cudaStreamSynchronize(s) == cudaSuccess ? PE_OK : PE_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int polyeval_track_defaults(int precision, pe_track_params *prm) {
+  if (!prm || !valid_precision(precision) || precision == PE_QD_INT) return PE_EINVAL;
+  const bool dd = precision != PE_F64;
+  prm->gamma_re = 0.5403023058681398;  // exp(i): a fixed point of the unit circle off every axis
+  prm->gamma_im = 0.8414709848078965;
+  prm->h_init = 0.02;
+  prm->h_min = dd ? 1e-14 : 1e-10;
+  prm->h_max = 0.1;
+  prm->corr_tol = dd ? 1e-12 : 1e-9;
+  prm->end_tol = dd ? 1e-26 : 1e-13;
+  prm->x_big = 1e8;
+  prm->max_corr = 3;
+  prm->max_end = 8;
+  prm->succ_grow = 3;
+  prm->max_iters = 100000;
+  return PE_OK;
+}
+
+int polyeval_bezout(const polyeval_t *h, double *count, int32_t *degrees) {
+  if (!h || h->batch || h->degrees.empty()) return PE_EINVAL;
+  double c = 1.0;
+  for (size_t i = 0; i < h->degrees.size(); i++) {
+    c *= h->degrees[i];
+    if (degrees) degrees[i] = h->degrees[i];
+  }
+  if (count) *count = c;
+  return PE_OK;
+}
+
+int polyeval_start_points(polyeval_t *h, int64_t first, int64_t P, void *points, void *stream) {
+  if (!trackable(h) || first < 0 || P < 0) return PE_EINVAL;
+  if (P == 0) return PE_OK;
+  if (!points) return PE_EINVAL;
+  int rc;
+  if ((rc = upload_degrees(h)) != PE_OK) return rc;
+  return pe::launch_start_points(h->dd, h->sys[0].n, static_cast<const int32_t *>(h->deg_dev.p), first, P,
+                                 static_cast<double *>(points), static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? PE_OK
+             : PE_ECUDA;
+}
+
+int polyeval_track(polyeval_t *h, const pe_track_params *prm, void *points, int64_t P, double *t, int32_t *status,
+                   int64_t *iterations, void *stream) {
+  if (iterations) *iterations = 0;
+  if (!trackable(h) || !params_ok(prm) || P < 0) return PE_EINVAL;
+  if (P > h->max_points) return PE_ERANGE;
+  if (P > 0 && !points) return PE_EINVAL;
+  return track(h, prm, static_cast<double *>(points), P, t, status, iterations, static_cast<cudaStream_t>(stream));
+}
+
+int polyeval_track_adaptive(polyeval_t *h_lo, polyeval_t *h_hi, const pe_track_params *prm_lo,
+                            const pe_track_params *prm_hi, void *points, int64_t P, int32_t *status,
+                            int64_t *escalated, void *stream) {
+  if (escalated) *escalated = 0;
+  if (!trackable(h_lo) || !trackable(h_hi) || h_lo->dd || !h_hi->dd || !params_ok(prm_lo) || !params_ok(prm_hi) ||
+      P < 0)
+    return PE_EINVAL;
+  if (h_lo->sys[0].n != h_hi->sys[0].n || h_lo->degrees != h_hi->degrees) return PE_EINVAL;
+  if (P > h_lo->max_points || P > h_hi->max_points) return PE_ERANGE;
+  if (P == 0) return PE_OK;
+  if (!points || !status) return PE_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int32_t n = h_hi->sys[0].n;
+  double *x = static_cast<double *>(points);
+  const int64_t count = static_cast<int64_t>(n) * P;
+  int rc;
+  if ((rc = ensure(h_lo->tr_x64, sizeof(double) * 2 * static_cast<size_t>(count))) ||
+      (rc = ensure(h_lo->tr_status, sizeof(int32_t) * static_cast<size_t>(P))) || (rc = track_scratch(h_hi, P)))
+    return rc;
+  double *x64 = static_cast<double *>(h_lo->tr_x64.p);
+  int32_t *st_lo = static_cast<int32_t *>(h_lo->tr_status.p);
+  // 1. every path in double precision
+  if (pe::launch_narrow_points(x, x64, count, s) != cudaSuccess) return PE_ECUDA;
+  if ((rc = track(h_lo, prm_lo, x64, P, nullptr, st_lo, nullptr, s)) != PE_OK) return rc;
+  std::vector<int32_t> st(static_cast<size_t>(P));
+  if (cudaMemcpy(st.data(), st_lo, sizeof(int32_t) * st.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PE_ECUDA;
+  std::vector<int64_t> redo;
+  for (int64_t q = 0; q < P; q++)
+    if (st[static_cast<size_t>(q)] != pe::kPathSuccess) redo.push_back(q);
+  const int64_t m = static_cast<int64_t>(redo.size());
+  // 2. the start points of the paths that did not succeed, set aside
+  if (m > 0) {
+    if ((rc = ensure(h_hi->tr_xc, sizeof(double) * 4 * static_cast<size_t>(n) * m)) ||
+        (rc = ensure(h_hi->tr_statc, sizeof(int32_t) * static_cast<size_t>(m))) ||
+        (rc = ensure(h_hi->tr_idx, sizeof(int64_t) * static_cast<size_t>(m))))
+      return rc;
+    if (cudaMemcpyAsync(h_hi->tr_idx.p, redo.data(), sizeof(int64_t) * redo.size(), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return PE_ECUDA;
+    if (pe::launch_move_paths(x, P, static_cast<double *>(h_hi->tr_xc.p), m, static_cast<const int64_t *>(h_hi->tr_idx.p),
+                              m, n, 4, false, s) != cudaSuccess)
+      return PE_ECUDA;
+  }
+  // 3. the double-precision endpoints, refined by Newton's method in double-double
+  if (pe::launch_widen_points(x64, x, count, s) != cudaSuccess) return PE_ECUDA;
+  for (int k = 0; k < 3; k++)
+    if ((rc = polyeval_newton(h_hi, x, P, h_hi->tr_f.p, h_hi->tr_J.p, nullptr, s)) != PE_OK) return rc;
+  if (cudaMemcpyAsync(status, st_lo, sizeof(int32_t) * static_cast<size_t>(P), cudaMemcpyDeviceToDevice, s) !=
+      cudaSuccess)
+    return PE_ECUDA;
+  // 4. the others tracked again from their start points in double-double
+  if (m > 0) {
+    if (m > h_hi->max_points) return PE_ERANGE;
+    double *xc = static_cast<double *>(h_hi->tr_xc.p);
+    int32_t *stc = static_cast<int32_t *>(h_hi->tr_statc.p);
+    if ((rc = track(h_hi, prm_hi, xc, m, nullptr, stc, nullptr, s)) != PE_OK) return rc;
+    const int64_t *idx = static_cast<const int64_t *>(h_hi->tr_idx.p);
+    if (pe::launch_move_paths(xc, m, x, P, idx, m, n, 4, true, s) != cudaSuccess ||
+        pe::launch_scatter_status(stc, status, idx, m, s) != cudaSuccess)
+      return PE_ECUDA;
+  }
+  if (escalated) *escalated = m;
+  return cudaStreamSynchronize(s) == cudaSuccess ? PE_OK : PE_ECUDA;
 }
 
 }  // extern "C"

@@ -137,4 +137,41 @@ cudaError_t launch_main_qd(const MainParams &p, int warps_per_block, size_t smem
 cudaError_t launch_finalize_qd(double *out_f, double *out_J, const double *scratch_f, const double *scratch_J,
                                int64_t f_components, int64_t J_components, int chunks, cudaStream_t s);
 
+// Path tracker (track.cu).  Phases of a path and its status (the status
+// values are the PE_PATH_* codes of the C ABI).
+constexpr int32_t kPhaseCorrect = 0, kPhasePredict = 1, kPhaseEnd = 2;
+constexpr int32_t kPathRunning = 0, kPathSuccess = 1, kPathFailed = 2, kPathDiverged = 3, kPathEndNotConverged = 4;
+
+struct TrackState {
+  double t;       // last accepted value of the continuation parameter
+  double t1;      // value the corrector works at
+  double h;       // step size
+  double dprev;   // previous corrector step size (contraction check)
+  int32_t phase, iter, succ, status;
+};
+
+struct TrackParams {
+  int32_t n;          // variables = polynomials
+  int64_t P;          // paths
+  double *J, *f;      // J_F [n][n][P] and F [n][P] at x (evaluator outputs), overwritten
+  double *x;          // [n][P] current points
+  double *xs;         // [n][P] last accepted point of each path
+  TrackState *st;     // [P]
+  const int32_t *deg; // [n] degrees of the start system x_i^(d_i) - 1
+  double gre, gim;    // gamma
+  double h_min, h_max, corr_tol, end_tol, x_big;
+  int32_t max_corr, max_end, succ_grow;
+  unsigned int *active;  // incremented once per path still running after a step
+};
+cudaError_t launch_track_init(bool dd, const TrackParams &p, double h_init, cudaStream_t s);
+cudaError_t launch_track_step(bool dd, const TrackParams &p, cudaStream_t s);
+cudaError_t launch_track_finish(const TrackState *st, int64_t P, double *t, int32_t *status, cudaStream_t s);
+cudaError_t launch_start_points(bool dd, int32_t n, const int32_t *deg, int64_t first, int64_t P, double *x,
+                                cudaStream_t s);
+cudaError_t launch_narrow_points(const double *dd, double *c64, int64_t count, cudaStream_t s);
+cudaError_t launch_widen_points(const double *c64, double *dd, int64_t count, cudaStream_t s);
+cudaError_t launch_move_paths(const double *src, int64_t P_src, double *dst, int64_t P_dst, const int64_t *idx,
+                              int64_t m, int32_t n, int words, bool scatter, cudaStream_t s);
+cudaError_t launch_scatter_status(const int32_t *src, int32_t *dst, const int64_t *idx, int64_t m, cudaStream_t s);
+
 }  // namespace pe

@@ -1,0 +1,96 @@
+// Solution of one point's linear system J y = b by LU decomposition with
+// partial pivoting, by one warp, in place in the structure-of-arrays layout
+// the evaluator writes (J [n][n][P], b [n][P], point index fastest).  Used
+// by the Newton step (newton.cu) and the path tracker (track.cu).
+//
+// In elimination step k the lanes take the columns j > k of the trailing
+// rows (lane j, j + 32, ...), the pivot is the row of largest |J[i][k]| (by
+// the leading parts; the smallest index on ties) found by a warp-wide
+// arg-max, the multipliers are formed by the lanes that own their rows, and
+// the back substitution reduces each row's dot product across the warp.
+// On return J holds the factors (unit lower triangle below the diagonal,
+// after the row exchanges) and b the solution y.
+#pragma once
+
+#include <cstdint>
+
+#include "cplx.cuh"
+
+namespace pe {
+
+// Element accessors of one point q in the [.][P] layouts.
+template <class C>
+struct PointView {
+  double *J, *b;
+  int n;
+  size_t P;
+  int64_t q;
+  __device__ double *Jel(int i, int j) const { return J + ((static_cast<size_t>(i) * n + j) * P + q) * C::kDoubles; }
+  __device__ double *bel(int i) const { return b + (static_cast<size_t>(i) * P + q) * C::kDoubles; }
+};
+
+// Returns true (warp-uniform) when a pivot column is exactly zero; b is then
+// left partly eliminated.
+template <class C>
+__device__ bool lu_solve(const PointView<C> &v, int lane) {
+  const int n = v.n;
+  for (int k = 0; k < n; k++) {
+    double best = -1.0;
+    int piv = n;
+    for (int i = k + lane; i < n; i += 32) {
+      const double m = C::load(v.Jel(i, k)).abs_hi();
+      if (m > best) {
+        best = m;
+        piv = i;
+      }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+      const double ob = __shfl_xor_sync(kAll, best, d);
+      const int op = __shfl_xor_sync(kAll, piv, d);
+      if (ob > best || (ob == best && op < piv)) {
+        best = ob;
+        piv = op;
+      }
+    }
+    if (!(best > 0.0)) return true;  // warp-uniform
+    if (piv != k) {
+      for (int j = k + lane; j < n; j += 32) {
+        const C a = C::load(v.Jel(k, j)), c = C::load(v.Jel(piv, j));
+        c.store(v.Jel(k, j));
+        a.store(v.Jel(piv, j));
+      }
+      if (lane == 0) {
+        const C a = C::load(v.bel(k)), c = C::load(v.bel(piv));
+        c.store(v.bel(k));
+        a.store(v.bel(piv));
+      }
+      __syncwarp();
+    }
+    // multipliers l_i = J[i][k] / J[k][k] and the right-hand side
+    const C inv = C::recip(C::load(v.Jel(k, k)));
+    const C bk = C::load(v.bel(k));
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      const C l = C::mul(C::load(v.Jel(i, k)), inv);
+      l.store(v.Jel(i, k));
+      C::sub_mul(C::load(v.bel(i)), l, bk).store(v.bel(i));
+    }
+    __syncwarp();
+    // trailing update: lanes over the columns j > k
+    for (int j = k + 1 + lane; j < n; j += 32) {
+      const C u = C::load(v.Jel(k, j));
+      for (int i = k + 1; i < n; i++) C::sub_mul(C::load(v.Jel(i, j)), C::load(v.Jel(i, k)), u).store(v.Jel(i, j));
+    }
+    __syncwarp();
+  }
+  // back substitution, y overwrites b
+  for (int i = n - 1; i >= 0; i--) {
+    C s = C::zero();
+    for (int j = i + 1 + lane; j < n; j += 32) s = C::sub_mul(s, C::load(v.Jel(i, j)), C::load(v.bel(j)));
+    for (int d = 16; d > 0; d >>= 1) s = C::add2(s, s.shfl_down(d));
+    if (lane == 0) C::mul(C::add2(C::load(v.bel(i)), s).finish(), C::recip(C::load(v.Jel(i, i)))).store(v.bel(i));
+    __syncwarp();
+  }
+  return false;
+}
+
+}  // namespace pe

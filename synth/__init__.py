@@ -361,3 +361,25 @@ def gaussian_int_cdd(rng, size, lo=-3, hi=3, nonzero=True):
     out[:, 0] = re
     out[:, 2] = im
     return out
+
+
+def dense_system(seed, n, degrees):
+    """A square system whose polynomial i holds every monomial of total
+    degree <= degrees[i] in the n variables (the constant included), with
+    random complex double-double coefficients near the unit circle: generic,
+    so the total-degree homotopy has prod(degrees) finite regular solutions
+    (with probability one)."""
+    import itertools
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    polys = []
+    for d in degrees:
+        mons = []
+        for e in itertools.product(range(d + 1), repeat=n):
+            if sum(e) <= d:
+                pos = [v for v in range(n) if e[v] > 0]
+                mons.append((pos, [e[v] for v in pos]))
+        polys.append(mons)
+    M = sum(len(p) for p in polys)
+    return from_monomials(n, polys, random_cdd(rng, M))
+

@@ -1,0 +1,226 @@
+"""Path tracking on the GPU (polyeval_start_points, polyeval_track,
+polyeval_track_adaptive) against the tracking oracle and known solution sets.
+
+End points are compared as sets (the paths may meet the solutions in any
+order): every expected solution must have its own GPU end point within the
+tolerance.  Double-double end points are also checked by their exact
+residual |F(x*)| / S_F(x*) from the exact oracle.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import exact as E
+from oracle import track as T
+
+from _util import pe_precision
+
+pytestmark = pytest.mark.gpu
+
+TRACK_PRECS = ["dd", "ddint", "f64"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1201_0499_gb300 as pkg
+
+    pkg.load_library()
+    torch.cuda.set_device(0)
+
+
+def system_for(s, prec):
+    return s.as_fp64() if prec == "f64" else s
+
+
+def run_track(s, prec, prm=None):
+    """(end points [B, n] complex, raw end points [n, B, c], status [B], handle)."""
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+
+    B = int(np.prod(T.degrees(s)))
+    ev = pkg.PolyEval(system_for(s, prec), pe_precision(prec), max_points=B)
+    assert ev.bezout()[0] == B
+    x = ev.start_points(B)
+    status, t, it = ev.track(x, prm)
+    torch.cuda.synchronize()
+    assert ev.status() == pkg.PE_OK and it >= 1
+    raw = x.cpu().numpy()
+    w = raw.shape[-1] // 2
+    z = (raw[..., 0] + 1j * raw[..., w]).T
+    return z, raw, status.cpu().numpy(), t.cpu().numpy(), ev
+
+
+def match(found, want, tol):
+    found = [np.asarray(f) for f in found]
+    used = set()
+    for w in want:
+        d = [(np.max(np.abs(f - np.asarray(w))), i) for i, f in enumerate(found) if i not in used]
+        best, i = min(d)
+        if best > tol:
+            return False
+        used.add(i)
+    return True
+
+
+def exact_residual(s, raw):
+    """max over paths and polynomials of |F(x*)| / S_F(x*), exactly."""
+    worst = 0.0
+    for q in range(raw.shape[1]):
+        f, _ = E.evaluate_point(s, raw, q)
+        Sf, _ = E.scales_point(s, raw, q)
+        for p in range(s.n_polys):
+            worst = max(worst, E.cx_abs(f[p]) / Sf[p])
+    return worst
+
+
+def univariate(seed, deg):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = rng.standard_normal(deg + 1) + 1j * rng.standard_normal(deg + 1)
+    mons = [([0], [k]) if k else ([], []) for k in range(deg + 1)]
+    return synth.from_monomials(1, [mons], [[z.real, 0, z.imag, 0] for z in c]), c
+
+
+@pytest.mark.parametrize("prec", TRACK_PRECS)
+def test_track_univariate_matches_numpy_roots(prec):
+    s, c = univariate(611, 7)
+    z, raw, st, t, _ = run_track(s, prec)
+    assert np.all(st == 1) and np.all(t == 1.0)
+    assert match(list(z), [[r] for r in np.roots(c[::-1])], 1e-9)
+
+
+@pytest.mark.parametrize("prec", TRACK_PRECS)
+def test_track_decoupled_product_set(prec):
+    r0 = [0.5 + 0.25j, -1.0 + 0.5j, 0.2 - 1.1j]
+    r1 = [1.5j, -0.75]
+    polys, coef = [], []
+    for v, roots in ((0, r0), (1, r1)):
+        c = np.array([1.0 + 0j])
+        for r in roots:
+            c = np.convolve(c, [1.0, -r])
+        mons = []
+        for k, a in enumerate(c):
+            e = len(roots) - k
+            mons.append(([v], [e]) if e else ([], []))
+            coef.append([a.real, 0, a.imag, 0])
+        polys.append(mons)
+    s = synth.from_monomials(2, polys, coef)
+    z, raw, st, _, _ = run_track(s, prec)
+    assert len(st) == 6 and np.all(st == 1)
+    assert match(list(z), list(itertools.product(r0, r1)), 1e-9)
+
+
+@pytest.mark.parametrize("prec", TRACK_PRECS)
+@pytest.mark.parametrize("case", [(612, 3, [2, 2, 2]), (613, 4, [2, 3, 1, 2])], ids=["n3_deg222", "n4_deg2312"])
+def test_track_generic_matches_oracle(prec, case):
+    seed, n, degs = case
+    s = synth.dense_system(seed, n, degs)
+    ref = T.solve_system(s.as_fp64() if prec == "f64" else s)
+    assert all(stv == T.SUCCESS for _, stv in ref)
+    z, raw, st, _, _ = run_track(s, prec)
+    assert len(st) == len(ref) and np.all(st == 1)
+    assert match(list(z), [x for x, _ in ref], 1e-8)
+    if prec != "f64":
+        assert exact_residual(s, raw) <= 1e-24
+
+
+def test_track_start_points_on_device():
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+
+    s = synth.dense_system(614, 3, [2, 3, 2])
+    for prec in ("dd", "f64"):
+        ev = pkg.PolyEval(system_for(s, prec), pe_precision(prec), max_points=12)
+        assert ev.bezout() == (12.0, [2, 3, 2])
+        x = ev.start_points(7, first=5)
+        torch.cuda.synchronize()
+        raw = x.cpu().numpy()
+        w = raw.shape[-1] // 2
+        want = T.start_points([2, 3, 2])[5:12]
+        for j in range(7):
+            for i in range(3):
+                assert abs(complex(raw[i, j, 0], raw[i, j, w]) - want[j][i]) < 1e-15
+                if w == 2:
+                    assert raw[i, j, 1] == 0.0 and raw[i, j, 3] == 0.0
+
+
+def test_track_dense_six_quadrics():
+    """64 paths of a generic system of six quadrics in six variables, in
+    double-double: all succeed at distinct end points with tiny residuals."""
+    s = synth.dense_system(615, 6, [2] * 6)
+    z, raw, st, _, _ = run_track(s, "dd")
+    assert len(st) == 64 and np.all(st == 1)
+    d = np.abs(z[:, None, :] - z[None, :, :]).max(axis=2) + np.eye(64)
+    assert d.min() > 1e-6
+    assert exact_residual(s, raw) <= 1e-24
+
+
+@pytest.mark.parametrize("hi", ["dd", "ddint"])
+def test_track_adaptive_precision(hi):
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+
+    s = synth.dense_system(616, 4, [2, 2, 3, 1])
+    B = 12
+    lo = pkg.PolyEval(s.as_fp64(), pkg.PE_F64, max_points=B)
+    hh = pkg.PolyEval(s, pe_precision(hi), max_points=B)
+    prm_lo = pkg.polyeval_track_defaults(pkg.PE_F64)
+    prm_hi = pkg.polyeval_track_defaults(pe_precision(hi))
+    ref = T.solve_system(s.as_fp64())
+    for force in (False, True):
+        x = hh.start_points(B)
+        status = torch.empty(B, dtype=torch.int32, device="cuda")
+        p_lo = prm_lo
+        if force:  # a double-precision end tolerance no double can meet: every path escalates
+            p_lo = pkg.polyeval_track_defaults(pkg.PE_F64)
+            p_lo.end_tol = 1e-300
+            p_lo.max_end = 2
+        esc = pkg.polyeval_track_adaptive(lo.handle, hh.handle, p_lo, prm_hi, x, B, status)
+        torch.cuda.synchronize()
+        st = status.cpu().numpy()
+        raw = x.cpu().numpy()
+        assert np.all(st == 1)
+        assert esc == B if force else 0 <= esc < B
+        z = (raw[..., 0] + 1j * raw[..., 2]).T
+        assert match(list(z), [xx for xx, _ in ref], 1e-8)
+        assert exact_residual(s, raw) <= 1e-24
+
+
+def test_track_no_finite_solutions():
+    s = synth.from_monomials(2, [[([0, 1], [1, 1]), ([], [])], [([0, 1], [1, 1]), ([], [])]],
+                             [[1, 0, 0, 0], [-1, 0, 0, 0], [1, 0, 0, 0], [-2, 0, 0, 0]])
+    _, _, st, _, _ = run_track(s, "f64")
+    assert np.all(st != 1) and np.all(st != 0)
+
+
+def test_track_rejections():
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+
+    rect = synth.from_monomials(3, [[([0], [1])], [([1], [2])]], [[1, 0, 0, 0], [1, 0, 0, 0]])
+    ev = pkg.PolyEval(rect, pkg.PE_DD, max_points=4)
+    with pytest.raises(pkg.PolyEvalError) as e:
+        ev.start_points(4)
+    assert e.value.code == pkg.PE_EINVAL
+    const = synth.from_monomials(2, [[([0], [1])], [([], [])]], [[1, 0, 0, 0], [1, 0, 0, 0]])
+    ev = pkg.PolyEval(const, pkg.PE_DD, max_points=4)
+    with pytest.raises(pkg.PolyEvalError) as e:
+        ev.track(torch.zeros((2, 4, 4), dtype=torch.float64, device="cuda"))
+    assert e.value.code == pkg.PE_EINVAL
+    s = synth.dense_system(617, 2, [2, 2])
+    evq = pkg.PolyEval(s, pkg.PE_QD_INT, max_points=4)
+    with pytest.raises(pkg.PolyEvalError) as e:
+        pkg.polyeval_start_points(evq.handle, 0, 4, torch.zeros((2, 4, 8), dtype=torch.float64, device="cuda"))
+    assert e.value.code == pkg.PE_EINVAL
+    ev = pkg.PolyEval(s, pkg.PE_DD, max_points=2)
+    with pytest.raises(pkg.PolyEvalError) as e:
+        ev.track(torch.zeros((2, 4, 4), dtype=torch.float64, device="cuda"))
+    assert e.value.code == pkg.PE_ERANGE
