@@ -304,6 +304,51 @@ class Workload:
         return ops * self.points, flops * self.points
 
 
+TRACK_N = 10  # variables of the path-tracking system (dense quadrics: 2^10 paths)
+
+
+def track_leg(pkg, torch):
+    """Solve a generic system of TRACK_N dense quadrics (every monomial of
+    degree <= 2) by following all 2^TRACK_N paths of the total-degree
+    homotopy: in double, in double-double (evaluations on the FP64 pipe and
+    on the integer pipes; linear solves in double with double-double
+    residuals), and adaptively (double, then double-double refinement and
+    re-tracking of failed paths)."""
+    s = synth.dense_system(synth.SEED_BASE + 700, TRACK_N, [2] * TRACK_N)
+    B = 2 ** TRACK_N
+    out = {"system": f"{TRACK_N} dense quadrics in {TRACK_N} variables (66 monomials each), {B} paths"}
+    hs = {}
+    for name, code in (("f64", pkg.PE_F64), ("dd", pkg.PE_DD), ("ddint", pkg.PE_DD_INT)):
+        ev = pkg.PolyEval(s.as_fp64() if code == pkg.PE_F64 else s, code, max_points=B)
+        hs[name] = ev
+        ev.track(ev.start_points(B))  # warm-up (allocates the tracker's scratch)
+        x = ev.start_points(B)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, _t, it = ev.track(x)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        out[name] = {"ms": el * 1e3, "paths_per_s": B / el, "iterations": it,
+                     "evals_per_s": it * B / el, "success": int((st == 1).sum().item())}
+    lo, hi = hs["f64"], hs["ddint"]
+    prm_lo, prm_hi = pkg.polyeval_track_defaults(pkg.PE_F64), pkg.polyeval_track_defaults(pkg.PE_DD)
+    status = torch.empty(B, dtype=torch.int32, device="cuda")
+    x = hi.start_points(B)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    esc = pkg.polyeval_track_adaptive(lo.handle, hi.handle, prm_lo, prm_hi, x, B, status)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    out["adaptive"] = {"ms": el * 1e3, "paths_per_s": B / el, "escalated_to_dd": esc,
+                       "success": int((status == 1).sum().item()),
+                       "what": "every path in double, end points refined by 3 Newton steps in double-double "
+                               "(integer-pipe evaluation), failed paths tracked again in double-double "
+                               "(polyeval_track_adaptive)"}
+    for ev in hs.values():
+        ev.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,6 +363,7 @@ def main():
                     help="skip polyeval_autotune (launch choices from the built-in heuristic)")
     ap.add_argument("--graph", action="store_true",
                     help="replay the evaluation from a captured CUDA graph in the timed steps")
+    ap.add_argument("--no-tracker", action="store_true", help="skip the path-tracking leg")
     ap.add_argument("--config", type=int, default=CONFIG_INDEX, choices=[2, 3, 4, 5],
                     help="workload (default 2, the benchmark workload; 3, 4, 5: the larger and ragged ones)")
     args = ap.parse_args()
@@ -491,6 +537,11 @@ def main():
                          "K3 one thread per output, complex double-double (PE_PAPER_KERNELS)"}
         ev_paper.close()
 
+    # path tracking on top of the evaluation (total-degree homotopy)
+    tracker = None
+    if args.config == CONFIG_INDEX and not args.no_tracker:
+        tracker = track_leg(pkg, torch)
+
     # end to end through the public API: pinned host in, pinned host out
     for _ in range(max(args.warmup, 1)):
         wl.eval_host(prim)
@@ -555,6 +606,7 @@ def main():
                              "256-bit integer block floating point, sums in 224-bit integer accumulators"},
             "fp64_peak_frac": achieved_tflops / peak_nominal,
             "newton_step": newton,
+            "path_tracker": tracker,
             "paper_three_kernels": paper,
             "clocks": clocks,
         }

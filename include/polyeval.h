@@ -361,6 +361,12 @@ PE_API int polyeval_eval_noalloc(const pe_system *dev_sys, int32_t max_k, int32_
  * (H_x v = -H_t, t1 = min(t + h, 1)), step size doubled after succ_grow
  * accepted steps in a row (at most h_max), and at t = 1 Newton's method on
  * F until max|dx| <= end_tol max(1, max|x|) (at most max_end steps).
+ * With `mixed` set, a double-double tracker keeps the homotopy, residuals and
+ * points in double-double but solves its linear systems in double from the
+ * leading parts of H_x (each Newton step is then a step of iterative
+ * refinement), which takes about a tenth of the FP64 work of a double-double
+ * solve; it applies when a path's n x n system in double fits the warp's
+ * shared memory (n <= 77), larger systems are solved in double-double.
  */
 typedef struct {
   double gamma_re, gamma_im; /* gamma (nonzero)                                   */
@@ -368,6 +374,7 @@ typedef struct {
   double corr_tol, end_tol;  /* relative step tolerances (see above)              */
   double x_big;              /* max|x| above which a path counts as diverging     */
   int32_t max_corr, max_end, succ_grow;
+  int32_t mixed;             /* double-double handles: solve in double (see above) */
   int64_t max_iters;         /* iterations (evaluations) of the whole batch, at most */
 } pe_track_params;
 
@@ -416,7 +423,8 @@ PE_API int polyeval_track(polyeval_t *h, const pe_track_params *prm, void *point
  * of the system); the end points of the paths that succeed are refined by
  * three Newton steps in double-double (h_hi, a PE_DD or PE_DD_INT handle of
  * the same system), and only the paths that did not succeed are tracked
- * again, from their start points, in double-double.
+ * again, from their start points, in double-double (with their linear systems
+ * in double-double whatever prm_hi->mixed says: these are the hard paths).
  *   points     device [n][P] pe_cdd: start points in, end points out
  *   status     device [P]: PE_PATH_* of each path (of its final tracking)
  *   escalated  host, or NULL: the number of paths tracked in double-double

@@ -79,6 +79,7 @@ class pe_track_params(ctypes.Structure):
         ("max_corr", ctypes.c_int32),
         ("max_end", ctypes.c_int32),
         ("succ_grow", ctypes.c_int32),
+        ("mixed", ctypes.c_int32),
         ("max_iters", ctypes.c_int64),
     ]
 

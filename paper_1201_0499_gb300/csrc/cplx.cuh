@@ -96,4 +96,18 @@ struct C64 {
 };
 
 
+// Conversions between the two (double-double to double keeps the leading
+// parts, the nearest doubles of a renormalised value).
+template <class L, class C>
+__device__ __forceinline__ L convert(const C &x);
+template <>
+__device__ __forceinline__ CDD convert<CDD, CDD>(const CDD &x) { return x; }
+template <>
+__device__ __forceinline__ C64 convert<C64, C64>(const C64 &x) { return x; }
+template <>
+__device__ __forceinline__ C64 convert<C64, CDD>(const CDD &x) { return C64{x.re.h, x.im.h}; }
+template <>
+__device__ __forceinline__ CDD convert<CDD, C64>(const C64 &x) { return CDD{dd{x.re, 0.0}, dd{x.im, 0.0}}; }
+
 }  // namespace pe
+

@@ -1085,6 +1085,7 @@ int track(polyeval *h, const pe_track_params *prm, double *x, int64_t P, double 
   tp.max_corr = prm->max_corr;
   tp.max_end = prm->max_end;
   tp.succ_grow = prm->succ_grow;
+  tp.mixed = prm->mixed != 0;
   tp.active = static_cast<unsigned *>(h->tr_active.p);
   if (pe::launch_track_init(h->dd, tp, prm->h_init, s) != cudaSuccess) return PE_ECUDA;
   int64_t it = 0;
@@ -1118,12 +1119,13 @@ int polyeval_track_defaults(int precision, pe_track_params *prm) {
   prm->h_init = 0.02;
   prm->h_min = dd ? 1e-14 : 1e-10;
   prm->h_max = 0.1;
-  prm->corr_tol = dd ? 1e-12 : 1e-9;
+  prm->corr_tol = 1e-9;
   prm->end_tol = dd ? 1e-26 : 1e-13;
   prm->x_big = 1e8;
   prm->max_corr = 3;
   prm->max_end = 8;
   prm->succ_grow = 3;
+  prm->mixed = dd ? 1 : 0;
   prm->max_iters = 100000;
   return PE_OK;
 }
@@ -1216,7 +1218,9 @@ int polyeval_track_adaptive(polyeval_t *h_lo, polyeval_t *h_hi, const pe_track_p
     if (m > h_hi->max_points) return PE_ERANGE;
     double *xc = static_cast<double *>(h_hi->tr_xc.p);
     int32_t *stc = static_cast<int32_t *>(h_hi->tr_statc.p);
-    if ((rc = track(h_hi, prm_hi, xc, m, nullptr, stc, nullptr, s)) != PE_OK) return rc;
+    pe_track_params full = *prm_hi;
+    full.mixed = 0;
+    if ((rc = track(h_hi, &full, xc, m, nullptr, stc, nullptr, s)) != PE_OK) return rc;
     const int64_t *idx = static_cast<const int64_t *>(h_hi->tr_idx.p);
     if (pe::launch_move_paths(xc, m, x, P, idx, m, n, 4, true, s) != cudaSuccess ||
         pe::launch_scatter_status(stc, status, idx, m, s) != cudaSuccess)

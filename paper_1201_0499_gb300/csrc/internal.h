@@ -161,6 +161,7 @@ struct TrackParams {
   double gre, gim;    // gamma
   double h_min, h_max, corr_tol, end_tol, x_big;
   int32_t max_corr, max_end, succ_grow;
+  int32_t mixed;      // double-double paths: linear systems solved in double
   unsigned int *active;  // incremented once per path still running after a step
 };
 cudaError_t launch_track_init(bool dd, const TrackParams &p, double h_init, cudaStream_t s);

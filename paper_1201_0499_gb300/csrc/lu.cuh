@@ -1,7 +1,10 @@
 // Solution of one point's linear system J y = b by LU decomposition with
-// partial pivoting, by one warp, in place in the structure-of-arrays layout
-// the evaluator writes (J [n][n][P], b [n][P], point index fastest).  Used
-// by the Newton step (newton.cu) and the path tracker (track.cu).
+// partial pivoting, by one warp, in place: either in the structure-of-arrays
+// layout the evaluator writes (J [n][n][P], b [n][P], point index fastest;
+// PointView) or in a copy in the warp's shared memory (row-major [n][n] and
+// [n]; SmemView), which turns the chains of dependent global loads and stores
+// of the elimination into shared-memory accesses.  Used by the Newton step
+// (newton.cu) and the path tracker (track.cu).
 //
 // In elimination step k the lanes take the columns j > k of the trailing
 // rows (lane j, j + 32, ...), the pivot is the row of largest |J[i][k]| (by
@@ -29,10 +32,31 @@ struct PointView {
   __device__ double *bel(int i) const { return b + (static_cast<size_t>(i) * P + q) * C::kDoubles; }
 };
 
+// One point's system in shared memory: A row-major [n][n], b [n].
+template <class C>
+struct SmemView {
+  double *A, *b;
+  int n;
+  __device__ double *Jel(int i, int j) const { return A + (static_cast<size_t>(i) * n + j) * C::kDoubles; }
+  __device__ double *bel(int i) const { return b + static_cast<size_t>(i) * C::kDoubles; }
+};
+
+// Bytes of shared memory one warp needs for an n x n system and the largest
+// n staged in shared memory (larger systems are solved in global memory).
+template <class C>
+__host__ __device__ constexpr size_t smem_lu_bytes(int n) {
+  return static_cast<size_t>(n) * (n + 1) * C::kDoubles * sizeof(double);
+}
+constexpr size_t kSmemLuMax = 96 * 1024;
+
+// Warps per block for the shared-memory variant: four when four systems fit
+// in 192 KiB, else one.
+inline int smem_lu_warps(size_t per_warp) { return per_warp * 4 <= 192 * 1024 ? 4 : 1; }
+
 // Returns true (warp-uniform) when a pivot column is exactly zero; b is then
 // left partly eliminated.
-template <class C>
-__device__ bool lu_solve(const PointView<C> &v, int lane) {
+template <class C, class V>
+__device__ bool lu_solve(const V &v, int lane) {
   const int n = v.n;
   for (int k = 0; k < n; k++) {
     double best = -1.0;
@@ -93,4 +117,62 @@ __device__ bool lu_solve(const PointView<C> &v, int lane) {
   return false;
 }
 
+// One thread per point, for small n: the whole elimination by the thread that
+// owns the point, on its own elements of the [.][P] layout (a warp's 32
+// threads touch 32 consecutive points of every element, so each access is
+// coalesced and every lane does useful arithmetic -- the warp-per-point
+// version leaves 32 - n lanes idle, and on GB300 an FP64 warp instruction
+// costs the FP64 pipe the same whatever its active lanes).  Elements are
+// read and written as L at the start of each slot of the view (L may be
+// narrower than the view's element).  Full rows are exchanged.  A thread's
+// elimination is a long dependent chain, so this pays only when enough
+// points run at once to keep every SM's FP64 pipe busy: n <= kThreadLuMaxN
+// and at least kThreadLuMinP points (below that the warp-per-point solve,
+// which spreads each point over n lanes, finishes first).
+constexpr int kThreadLuMaxN = 16;
+constexpr int64_t kThreadLuMinP = 4096;
+inline bool thread_lu(int n, int64_t P) { return n <= kThreadLuMaxN && P >= kThreadLuMinP; }
+
+template <class L, class V>
+__device__ bool lu_solve_thread(const V &v) {
+  const int n = v.n;
+  for (int k = 0; k < n; k++) {
+    double best = -1.0;
+    int piv = k;
+    for (int i = k; i < n; i++) {
+      const double m = L::load(v.Jel(i, k)).abs_hi();
+      if (m > best) {
+        best = m;
+        piv = i;
+      }
+    }
+    if (!(best > 0.0)) return true;
+    if (piv != k) {
+      for (int j = 0; j < n; j++) {
+        const L a = L::load(v.Jel(k, j)), c = L::load(v.Jel(piv, j));
+        c.store(v.Jel(k, j));
+        a.store(v.Jel(piv, j));
+      }
+      const L a = L::load(v.bel(k)), c = L::load(v.bel(piv));
+      c.store(v.bel(k));
+      a.store(v.bel(piv));
+    }
+    const L inv = L::recip(L::load(v.Jel(k, k)));
+    const L bk = L::load(v.bel(k));
+    for (int i = k + 1; i < n; i++) {
+      const L l = L::mul(L::load(v.Jel(i, k)), inv);
+      l.store(v.Jel(i, k));
+      L::sub_mul(L::load(v.bel(i)), l, bk).store(v.bel(i));
+      for (int j = k + 1; j < n; j++) L::sub_mul(L::load(v.Jel(i, j)), l, L::load(v.Jel(k, j))).store(v.Jel(i, j));
+    }
+  }
+  for (int i = n - 1; i >= 0; i--) {
+    L s = L::load(v.bel(i));
+    for (int j = i + 1; j < n; j++) s = L::sub_mul(s, L::load(v.Jel(i, j)), L::load(v.bel(j)));
+    L::mul(s.finish(), L::recip(L::load(v.Jel(i, i)))).store(v.bel(i));
+  }
+  return false;
+}
+
 }  // namespace pe
+

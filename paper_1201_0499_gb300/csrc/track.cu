@@ -21,6 +21,15 @@
 //            (success) or max_end steps (endpoint not converged).
 // After succ_grow accepted steps in a row the step size doubles (up to h_max).
 // Paths whose max|x| exceeds x_big are marked diverged.
+//
+// Mixed precision (double-double tracking with `mixed` set, systems whose
+// matrix fits in shared memory): the homotopy, the right-hand sides and the
+// points stay in double-double, the linear systems are solved in double from
+// the leading parts of H_x.  Each corrector step is then a step of iterative
+// refinement, whose error falls by about u cond(H_x) (u = 2^-53) per step, and
+// the step kernel runs about a tenth of the FP64 instructions of a
+// double-double LU -- on GB300, whose FP64 pipe issues a warp instruction in
+// 16 cycles whatever the active lanes, that is most of a tracker iteration.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -52,51 +61,77 @@ __device__ __forceinline__ double warp_max(double v) {
 
 }  // namespace
 
-template <class C>
-__global__ void track_step(const TrackParams p) {
-  const int lane = threadIdx.x & 31;
-  const int64_t q = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if (q >= p.P) return;  // warp-uniform
+// The threads that advance one path: a whole warp (lanes split the columns
+// and rows, warp-wide maxima) or a single thread (small n; lu.cuh).
+struct WarpGroup {
+  int lane;
+  static constexpr int size = 32;
+  __device__ double max(double v) const { return warp_max(v); }
+  __device__ void sync() const { __syncwarp(); }
+};
+struct ThreadGroup {
+  static constexpr int lane = 0;
+  static constexpr int size = 1;
+  __device__ double max(double v) const { return v; }
+  __device__ void sync() const {}
+};
+
+// One step of path q.  C: the tracker's arithmetic; L: that of the linear
+// solve (C, or C64 for mixed precision).  kSmem (warp groups only): the
+// system is staged in the warp's shared memory, else it is formed in place
+// in the evaluator's J and f (as L at the start of each element's slot).
+template <class C, class L, bool kSmem, class G>
+__device__ void track_path(const TrackParams &p, int64_t q, const G grp, double *sm) {
   TrackState s = p.st[q];
-  if (s.status != kPathRunning) return;  // warp-uniform
-  const int n = p.n;
+  if (s.status != kPathRunning) return;  // uniform over the group
+  const int n = p.n, lane = grp.lane;
   const size_t P = static_cast<size_t>(p.P);
-  const PointView<C> v{p.J, p.f, n, P, q};
+  const PointView<C> g{p.J, p.f, n, P, q};
+  const SmemView<L> sv{sm, sm + static_cast<size_t>(n) * n * L::kDoubles, n};
+  auto Ael = [&](int i, int j) { return kSmem ? sv.Jel(i, j) : g.Jel(i, j); };
+  auto bel = [&](int i) { return kSmem ? sv.bel(i) : g.bel(i); };
   auto Xel = [&](double *base, int i) { return base + (static_cast<size_t>(i) * P + q) * C::kDoubles; };
   const C gamma = C::make(p.gre, p.gim);
 
-  // the homotopy at (x, tt): matrix H_x in J, right-hand side in f
+  // the homotopy at (x, tt): matrix H_x, right-hand side
   const bool predict = s.phase == kPhasePredict;
   const double tt = predict ? s.t : (s.phase == kPhaseEnd ? 1.0 : s.t1);
   const C a = C::scale(gamma, 1.0 - tt);  // gamma (1 - t)
+  const L al = convert<L>(a);
   for (int i = 0; i < n; i++) {
-    for (int j = lane; j < n; j += 32) {
-      C e = C::scale(C::load(v.Jel(i, j)), tt);
+    for (int j = lane; j < n; j += G::size) {
+      L e = L::scale(convert<L>(C::load(g.Jel(i, j))), tt);
       if (j == i) {
-        const C xi = C::load(Xel(p.x, i));
+        const L xi = convert<L>(C::load(Xel(p.x, i)));
         const int d = p.deg[i];
-        e = C::add2(e, C::mul(a, C::scale(cpow(xi, d - 1), static_cast<double>(d)))).finish();
+        e = L::add2(e, L::mul(al, L::scale(cpow(xi, d - 1), static_cast<double>(d)))).finish();
       }
-      e.store(v.Jel(i, j));
+      e.store(Ael(i, j));
     }
   }
-  for (int i = lane; i < n; i += 32) {
+  for (int i = lane; i < n; i += G::size) {
     const C xi = C::load(Xel(p.x, i));
-    const C G = C::sub(cpow(xi, p.deg[i]), C::make(1.0, 0.0));
-    const C F = C::load(v.bel(i));
+    const C Gi = C::sub(cpow(xi, p.deg[i]), C::make(1.0, 0.0));
+    const C F = C::load(g.bel(i));
     C rhs;
     if (predict)  // -H_t = gamma G - F
-      rhs = C::sub(C::mul(gamma, G), F);
+      rhs = C::sub(C::mul(gamma, Gi), F);
     else  // -H = -(a G + t F)
-      rhs = C::add2(C::mul(a, G), C::scale(F, tt)).finish().neg();
-    rhs.store(v.bel(i));
+      rhs = C::add2(C::mul(a, Gi), C::scale(F, tt)).finish().neg();
+    convert<L>(rhs).store(bel(i));
   }
-  __syncwarp();
+  grp.sync();
 
-  const bool singular = lu_solve<C>(v, lane);
+  bool singular;
+  if constexpr (G::size == 1)
+    singular = lu_solve_thread<L>(g);
+  else if constexpr (kSmem)
+    singular = lu_solve<L>(sv, lane);
+  else
+    singular = lu_solve<L>(PointView<L>{p.J, p.f, n, P, q}, lane);
 
   auto restore = [&]() {  // x <- last accepted point
-    for (int i = lane; i < n; i += 32) C::load(Xel(p.xs, i)).store(Xel(p.x, i));
+    for (int i = lane; i < n; i += G::size) C::load(Xel(p.xs, i)).store(Xel(p.x, i));
   };
   auto reject = [&]() {
     restore();
@@ -115,22 +150,22 @@ __global__ void track_step(const TrackParams p) {
   } else if (predict) {
     s.t1 = fmin(s.t + s.h, 1.0);
     const double dt = s.t1 - s.t;
-    for (int i = lane; i < n; i += 32)
-      C::add2(C::load(Xel(p.x, i)), C::scale(C::load(v.bel(i)), dt)).finish().store(Xel(p.x, i));
+    for (int i = lane; i < n; i += G::size)
+      C::add2(C::load(Xel(p.x, i)), C::scale(convert<C>(L::load(bel(i))), dt)).finish().store(Xel(p.x, i));
     s.phase = kPhaseCorrect;
     s.iter = 0;
     s.dprev = INFINITY;
   } else {
     double dxn = 0.0, xn = 0.0;
-    for (int i = lane; i < n; i += 32) {
-      const C dx = C::load(v.bel(i));
+    for (int i = lane; i < n; i += G::size) {
+      const C dx = convert<C>(L::load(bel(i)));
       const C x1 = C::add2(C::load(Xel(p.x, i)), dx).finish();
       x1.store(Xel(p.x, i));
       dxn = fmax(dxn, dx.abs_hi());
       xn = fmax(xn, x1.abs_hi());
     }
-    dxn = warp_max(dxn);
-    xn = warp_max(xn);
+    dxn = grp.max(dxn);
+    xn = grp.max(xn);
     s.iter++;
     const double scale = fmax(1.0, xn);
     if (!(xn <= p.x_big)) {
@@ -142,7 +177,7 @@ __global__ void track_step(const TrackParams p) {
         s.status = kPathEndNotConverged;
     } else if (dxn <= p.corr_tol * scale) {  // accept
       s.t = s.t1;
-      for (int i = lane; i < n; i += 32) C::load(Xel(p.x, i)).store(Xel(p.xs, i));
+      for (int i = lane; i < n; i += G::size) C::load(Xel(p.x, i)).store(Xel(p.xs, i));
       if (++s.succ >= p.succ_grow) {
         s.h = fmin(2.0 * s.h, p.h_max);
         s.succ = 0;
@@ -155,11 +190,30 @@ __global__ void track_step(const TrackParams p) {
       s.dprev = dxn;
     }
   }
-  __syncwarp();
+  grp.sync();
   if (lane == 0) {
     p.st[q] = s;
     if (s.status == kPathRunning) atomicAdd(p.active, 1u);
   }
+}
+
+// One warp per path.
+template <class C, class L, bool kSmem>
+__global__ void track_step(const TrackParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t q = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (q >= p.P) return;  // warp-uniform
+  static_assert(kSmem || sizeof(L) == sizeof(C), "a mixed-precision warp solve needs the shared-memory copy");
+  double *sm = reinterpret_cast<double *>(smem_raw) + (threadIdx.x >> 5) * (smem_lu_bytes<L>(p.n) / sizeof(double));
+  track_path<C, L, kSmem>(p, q, WarpGroup{static_cast<int>(threadIdx.x & 31)}, sm);
+}
+
+// One thread per path (n <= kThreadLuMaxN).
+template <class C, class L>
+__global__ void track_step_thread(const TrackParams p) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= p.P) return;
+  track_path<C, L, false>(p, q, ThreadGroup{}, nullptr);
 }
 
 __global__ void track_init(const TrackParams p, double h_init, int words) {
@@ -266,15 +320,37 @@ cudaError_t launch_track_init(bool dd, const TrackParams &p, double h_init, cuda
   return cudaGetLastError();
 }
 
+template <class C, class L>
+cudaError_t launch_track_step_t(const TrackParams &p, cudaStream_t s) {
+  if (thread_lu(p.n, p.P)) {
+    const int threads = 32;
+    track_step_thread<C, L><<<static_cast<unsigned>((p.P + threads - 1) / threads), threads, 0, s>>>(p);
+    return cudaGetLastError();
+  }
+  const size_t per_warp = smem_lu_bytes<L>(p.n);
+  if (per_warp > kSmemLuMax) {
+    if (sizeof(L) != sizeof(C)) return launch_track_step_t<C, C>(p, s);  // too large to stage: full precision
+    const int threads = 128;
+    const int64_t blocks = (p.P * 32 + threads - 1) / threads;
+    track_step<C, C, false><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
+    return cudaGetLastError();
+  }
+  const int warps = smem_lu_warps(per_warp);
+  const size_t bytes = per_warp * warps;
+  if (bytes > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(track_step<C, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(bytes));
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t blocks = (p.P + warps - 1) / warps;
+  track_step<C, L, true><<<static_cast<unsigned>(blocks), warps * 32, bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_track_step(bool dd, const TrackParams &p, cudaStream_t s) {
   if (p.P <= 0) return cudaSuccess;
-  const int threads = 128;
-  const int64_t blocks = (p.P * 32 + threads - 1) / threads;
-  if (dd)
-    track_step<CDD><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
-  else
-    track_step<C64><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
-  return cudaGetLastError();
+  if (!dd) return launch_track_step_t<C64, C64>(p, s);
+  return p.mixed ? launch_track_step_t<CDD, C64>(p, s) : launch_track_step_t<CDD, CDD>(p, s);
 }
 
 cudaError_t launch_track_finish(const TrackState *st, int64_t P, double *t, int32_t *status, cudaStream_t s) {

@@ -160,6 +160,33 @@ def test_newton_converges_on_the_benchmark_system(prec):
     assert float(err.max()) < floor, float(err.max())
 
 
+@pytest.mark.parametrize("prec", ["dd", "f64"])
+def test_newton_large_batch_small_system(prec):
+    """4096 points of an 8 x 8 system: the one-thread-per-point solve.  The
+    step is checked against the exact Newton step at sampled points."""
+    n, P = 8, 4096
+    s = square_system(205, n, m=5, kmax=3, emax=3)
+    pts = synth.points(206, n, P)
+    if prec == "f64":
+        s, pts = s.as_fp64(), pts.copy()
+        pts[..., 1] = 0.0
+        pts[..., 3] = 0.0
+    x1, dx, norms = run_newton(s, pts, prec)
+    for q in (0, 1, 2047, 4095):
+        f, J, dx_exact, x1_exact = N.newton_step(s, pts, q)
+        g = [fr_dd(dx[i, q]) for i in range(n)]
+        res = 0.0
+        for i in range(n):
+            acc = f[i]
+            for j in range(n):
+                acc = N.c_add(acc, N.c_mul(J[i][j], g[j]))
+            res = max(res, cabs(acc))
+        Jn = max(sum(cabs(J[i][j]) for j in range(n)) for i in range(n))
+        eta = res / (Jn * max(cabs(gi) for gi in g) + max(cabs(fi) for fi in f))
+        assert eta <= BACKWARD_TOL[prec], (q, eta)
+        assert norms[q, 1] == pytest.approx(max(cabs(gi) for gi in g), rel=1e-12)
+
+
 def test_newton_rejects_non_square_and_batch():
     import torch
 

@@ -193,6 +193,58 @@ def test_track_adaptive_precision(hi):
         assert exact_residual(s, raw) <= 1e-24
 
 
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_track_double_double_linear_solves(mixed):
+    """Double-double tracking with the linear systems in double-double
+    (mixed = 0) or in double with double-double residuals (mixed = 1): the
+    same solutions, at double-double accuracy either way."""
+    import paper_1201_0499_gb300 as pkg
+
+    s = synth.dense_system(618, 3, [2, 3, 2])
+    prm = pkg.polyeval_track_defaults(pkg.PE_DD)
+    prm.mixed = mixed
+    z, raw, st, _, _ = run_track(s, "dd", prm)
+    assert np.all(st == 1)
+    assert match(list(z), [x for x, _ in T.solve_system(s)], 1e-8)
+    assert exact_residual(s, raw) <= 1e-24
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_track_large_system_two_paths(mixed):
+    """n = 60: 59 dense linear equations and one quadric (2 paths).  The
+    60 x 60 double-double system is too large for shared memory (solved in
+    place in global memory); in double it is staged."""
+    import paper_1201_0499_gb300 as pkg
+
+    n = 60
+    rng = np.random.Generator(np.random.PCG64(619))
+    polys = [[([j], [1]) for j in range(n)] + [([], [])] for _ in range(n - 1)]
+    polys.append([([0], [2]), ([1, 2], [1, 1]), ([3], [1]), ([], [])])
+    M = sum(len(p) for p in polys)
+    s = synth.from_monomials(n, polys, synth.random_cdd(rng, M))
+    prm = pkg.polyeval_track_defaults(pkg.PE_DD)
+    prm.mixed = mixed
+    z, raw, st, _, _ = run_track(s, "dd", prm)
+    assert len(st) == 2 and np.all(st == 1)
+    assert np.max(np.abs(z[0] - z[1])) > 1e-6
+    assert exact_residual(s, raw) <= 1e-24
+
+
+@pytest.mark.parametrize("prec", ["f64", "dd"])
+def test_track_large_batch_thread_per_path(prec):
+    """4096 paths (twelve quadrics): the batch is large enough for the
+    one-thread-per-path linear solves.  Every path succeeds at a distinct end
+    point; sampled end points have tiny exact residuals."""
+    s = synth.dense_system(620, 12, [2] * 12)
+    z, raw, st, _, _ = run_track(s, prec)
+    assert len(st) == 4096 and np.all(st == 1)
+    keys = np.round(np.concatenate([z.real, z.imag], axis=1), 6)
+    assert len(np.unique(keys, axis=0)) == 4096  # distinct end points
+    sample = raw[:, ::97]
+    tol = 1e-24 if prec == "dd" else 1e-12
+    assert exact_residual(system_for(s, prec), np.ascontiguousarray(sample)) <= tol
+
+
 def test_track_no_finite_solutions():
     s = synth.from_monomials(2, [[([0, 1], [1, 1]), ([], [])], [([0, 1], [1, 1]), ([], [])]],
                              [[1, 0, 0, 0], [-1, 0, 0, 0], [1, 0, 0, 0], [-2, 0, 0, 0]])
