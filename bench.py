@@ -307,6 +307,20 @@ class Workload:
 TRACK_N = 10  # variables of the path-tracking system (dense quadrics: 2^10 paths)
 
 
+def nominal_paper_flops(wl):
+    """Flops of one evaluation batch by the paper's operation counts: per
+    monomial 6k - 5 complex products (k - 1 for the common factor, 5k - 4 for
+    the Speelpenning gradient, value and coefficients, Sections 3.1-3.2) and
+    k + 1 complex sums, a complex double-double product counted as 88 flops
+    (four double-double products of 12 and two double-double sums of 20) and a
+    sum as 40; plus n (d - 2) products per point for the powers."""
+    s = wl.system
+    k = np.diff(s.mono_ptr)
+    per_point = float(np.sum(np.where(k > 0, (6 * k - 5) * 88 + (k + 1) * 40, 40)))
+    per_point += s.n_vars * max(s.max_exp - 2, 0) * 88
+    return per_point * wl.points
+
+
 def track_leg(pkg, torch):
     """Solve a generic system of TRACK_N dense quadrics (every monomial of
     degree <= 2) by following all 2^TRACK_N paths of the total-degree
@@ -364,6 +378,8 @@ def main():
     ap.add_argument("--graph", action="store_true",
                     help="replay the evaluation from a captured CUDA graph in the timed steps")
     ap.add_argument("--no-tracker", action="store_true", help="skip the path-tracking leg")
+    ap.add_argument("--only-tracker", action="store_true",
+                    help="run only the path-tracking leg and print its JSON object (for profiling the tracker)")
     ap.add_argument("--config", type=int, default=CONFIG_INDEX, choices=[2, 3, 4, 5],
                     help="workload (default 2, the benchmark workload; 3, 4, 5: the larger and ragged ones)")
     args = ap.parse_args()
@@ -386,6 +402,13 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    if args.only_tracker:
+        out = track_leg(pkg, torch)
+        if rank == 0:
+            print(json.dumps({"path_tracker": out}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     wl = Workload(args.config, rank, dev)
     prim = args.precision
     other = "ddint" if prim == "dd" else "dd"
@@ -474,6 +497,10 @@ def main():
     peaks = peaks_file()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_nominal = SMS * DFMA_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
+    # the paper's method at its own cost (6k - 5 complex products and k + 1
+    # complex sums per monomial, dd product 88 flops, dd sum 40): what the same
+    # evaluations would cost done the paper's way, per second of this kernel
+    nominal_flops = nominal_paper_flops(wl) if args.config != 4 else None
     fma_rate, probe_mhz = pkg.polyeval_fp64_peak(stream)
     peak_probe = 2 * fma_rate / 1e12
     issue_rate = ops_launch / (kern_avg_ms * 1e-3)
@@ -591,7 +618,9 @@ def main():
                          "peak_basis": f"nominal: {SMS} SMs x {DFMA_PER_SM_CLK} FP64 FMA/clk x 2 flops x {sm_max:.0f} MHz",
                          "peak_probe": peak_probe, "frac_of_probe": achieved_tflops / peak_probe,
                          "probe_sm_mhz": probe_mhz,
-                         "fp64_issue_frac": issue_rate / (SMS * DFMA_PER_SM_CLK * sm_max * 1e6)},
+                         "fp64_issue_frac": issue_rate / (SMS * DFMA_PER_SM_CLK * sm_max * 1e6),
+                         "paper_method_equiv_tflops": (nominal_flops / (kern_avg_ms * 1e-3) / 1e12
+                                                       if nominal_flops else None)},
             "fp64_path": {"evals_per_s": job_throughput(world, P, ms64), "ms_per_step": ms64},
             "dd_fp64_time_ratio": (ms_per_step if prim == "dd" else legs["dd"]) / ms64,
             ("int_pipe_path" if other == "ddint" else "fp64_dd_path"): {

@@ -365,8 +365,7 @@ PE_API int polyeval_eval_noalloc(const pe_system *dev_sys, int32_t max_k, int32_
  * points in double-double but solves its linear systems in double from the
  * leading parts of H_x (each Newton step is then a step of iterative
  * refinement), which takes about a tenth of the FP64 work of a double-double
- * solve; it applies when a path's n x n system in double fits the warp's
- * shared memory (n <= 77), larger systems are solved in double-double.
+ * solve (the handle keeps an n x n x P double scratch for it).
  */
 typedef struct {
   double gamma_re, gamma_im; /* gamma (nonzero)                                   */

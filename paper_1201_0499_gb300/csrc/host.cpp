@@ -91,7 +91,7 @@ struct polyeval {
   // path tracking (single square systems): degrees of the polynomials and
   // the tracker's scratch, allocated on first use
   std::vector<int32_t> degrees;
-  DeviceBuf deg_dev, tr_f, tr_J, tr_xs, tr_state, tr_active, tr_x64, tr_status, tr_xc, tr_statc, tr_idx;
+  DeviceBuf deg_dev, tr_f, tr_J, tr_xs, tr_state, tr_active, tr_x64, tr_status, tr_xc, tr_statc, tr_idx, tr_JL, tr_bL;
   struct Tuned {
     int64_t P;
     int chunks;
@@ -1085,7 +1085,13 @@ int track(polyeval *h, const pe_track_params *prm, double *x, int64_t P, double 
   tp.max_corr = prm->max_corr;
   tp.max_end = prm->max_end;
   tp.succ_grow = prm->succ_grow;
-  tp.mixed = prm->mixed != 0;
+  tp.mixed = prm->mixed != 0 && h->dd;
+  if (tp.mixed) {  // double copies of the systems, for warp solves outside shared memory
+    const size_t np = static_cast<size_t>(d.n) * static_cast<size_t>(P);
+    if ((rc = ensure(h->tr_JL, 16 * np * d.n)) || (rc = ensure(h->tr_bL, 16 * np))) return rc;
+    tp.JL = static_cast<double *>(h->tr_JL.p);
+    tp.bL = static_cast<double *>(h->tr_bL.p);
+  }
   tp.active = static_cast<unsigned *>(h->tr_active.p);
   if (pe::launch_track_init(h->dd, tp, prm->h_init, s) != cudaSuccess) return PE_ECUDA;
   int64_t it = 0;

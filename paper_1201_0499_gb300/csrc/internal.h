@@ -156,6 +156,7 @@ struct TrackParams {
   double *J, *f;      // J_F [n][n][P] and F [n][P] at x (evaluator outputs), overwritten
   double *x;          // [n][P] current points
   double *xs;         // [n][P] last accepted point of each path
+  double *JL, *bL;    // [n][n][P], [n][P] complex doubles: mixed-precision systems of warp solves in global memory
   TrackState *st;     // [P]
   const int32_t *deg; // [n] degrees of the start system x_i^(d_i) - 1
   double gre, gim;    // gamma

@@ -41,17 +41,16 @@ struct SmemView {
   __device__ double *bel(int i) const { return b + static_cast<size_t>(i) * C::kDoubles; }
 };
 
-// Bytes of shared memory one warp needs for an n x n system and the largest
-// n staged in shared memory (larger systems are solved in global memory).
+// Bytes of shared memory one warp needs for an n x n system, and the largest
+// such copy staged in shared memory: larger systems are solved in global
+// memory, where more warps per SM hide the latency (n = 32 in double-double,
+// 34 KiB per warp, ran slower staged than in place: 4 warps per SM).
 template <class C>
 __host__ __device__ constexpr size_t smem_lu_bytes(int n) {
   return static_cast<size_t>(n) * (n + 1) * C::kDoubles * sizeof(double);
 }
-constexpr size_t kSmemLuMax = 96 * 1024;
-
-// Warps per block for the shared-memory variant: four when four systems fit
-// in 192 KiB, else one.
-inline int smem_lu_warps(size_t per_warp) { return per_warp * 4 <= 192 * 1024 ? 4 : 1; }
+constexpr size_t kSmemLuMax = 16 * 1024;
+constexpr int kSmemLuWarps = 4;  // warps per block of the shared-memory variant
 
 // Returns true (warp-uniform) when a pivot column is exactly zero; b is then
 // left partly eliminated.

@@ -113,7 +113,7 @@ cudaError_t launch_newton_t(const NewtonParams &p, cudaStream_t s) {
     newton_lu<C, false><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
     return cudaGetLastError();
   }
-  const int warps = smem_lu_warps(per_warp);
+  const int warps = kSmemLuWarps;
   const size_t bytes = per_warp * warps;
   if (bytes > 48 * 1024) {
     const cudaError_t e =

@@ -22,10 +22,10 @@
 // After succ_grow accepted steps in a row the step size doubles (up to h_max).
 // Paths whose max|x| exceeds x_big are marked diverged.
 //
-// Mixed precision (double-double tracking with `mixed` set, systems whose
-// matrix fits in shared memory): the homotopy, the right-hand sides and the
-// points stay in double-double, the linear systems are solved in double from
-// the leading parts of H_x.  Each corrector step is then a step of iterative
+// Mixed precision (double-double tracking with `mixed` set): the homotopy,
+// the right-hand sides and the points stay in double-double, the linear
+// systems are solved in double from the leading parts of H_x (in shared
+// memory, in the tracker's double scratch, or in place per thread).  Each corrector step is then a step of iterative
 // refinement, whose error falls by about u cond(H_x) (u = 2^-53) per step, and
 // the step kernel runs about a tenth of the FP64 instructions of a
 // double-double LU -- on GB300, whose FP64 pipe issues a warp instruction in
@@ -78,8 +78,9 @@ struct ThreadGroup {
 
 // One step of path q.  C: the tracker's arithmetic; L: that of the linear
 // solve (C, or C64 for mixed precision).  kSmem (warp groups only): the
-// system is staged in the warp's shared memory, else it is formed in place
-// in the evaluator's J and f (as L at the start of each element's slot).
+// system is staged in the warp's shared memory; else a warp forms it in the
+// evaluator's J and f (L == C) or in the scratch p.JL, p.bL (L != C), and a
+// single thread in place in J and f (as L at the start of each slot).
 template <class C, class L, bool kSmem, class G>
 __device__ void track_path(const TrackParams &p, int64_t q, const G grp, double *sm) {
   TrackState s = p.st[q];
@@ -88,8 +89,11 @@ __device__ void track_path(const TrackParams &p, int64_t q, const G grp, double 
   const size_t P = static_cast<size_t>(p.P);
   const PointView<C> g{p.J, p.f, n, P, q};
   const SmemView<L> sv{sm, sm + static_cast<size_t>(n) * n * L::kDoubles, n};
-  auto Ael = [&](int i, int j) { return kSmem ? sv.Jel(i, j) : g.Jel(i, j); };
-  auto bel = [&](int i) { return kSmem ? sv.bel(i) : g.bel(i); };
+  // a warp's in-place system: the evaluator's arrays, or the double scratch
+  constexpr bool kScratch = G::size > 1 && !kSmem && sizeof(L) != sizeof(C);
+  const PointView<L> gl{kScratch ? p.JL : p.J, kScratch ? p.bL : p.f, n, P, q};
+  auto Ael = [&](int i, int j) { return kSmem ? sv.Jel(i, j) : G::size > 1 ? gl.Jel(i, j) : g.Jel(i, j); };
+  auto bel = [&](int i) { return kSmem ? sv.bel(i) : G::size > 1 ? gl.bel(i) : g.bel(i); };
   auto Xel = [&](double *base, int i) { return base + (static_cast<size_t>(i) * P + q) * C::kDoubles; };
   const C gamma = C::make(p.gre, p.gim);
 
@@ -128,7 +132,7 @@ __device__ void track_path(const TrackParams &p, int64_t q, const G grp, double 
   else if constexpr (kSmem)
     singular = lu_solve<L>(sv, lane);
   else
-    singular = lu_solve<L>(PointView<L>{p.J, p.f, n, P, q}, lane);
+    singular = lu_solve<L>(gl, lane);
 
   auto restore = [&]() {  // x <- last accepted point
     for (int i = lane; i < n; i += G::size) C::load(Xel(p.xs, i)).store(Xel(p.x, i));
@@ -203,7 +207,6 @@ __global__ void track_step(const TrackParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t q = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (q >= p.P) return;  // warp-uniform
-  static_assert(kSmem || sizeof(L) == sizeof(C), "a mixed-precision warp solve needs the shared-memory copy");
   double *sm = reinterpret_cast<double *>(smem_raw) + (threadIdx.x >> 5) * (smem_lu_bytes<L>(p.n) / sizeof(double));
   track_path<C, L, kSmem>(p, q, WarpGroup{static_cast<int>(threadIdx.x & 31)}, sm);
 }
@@ -329,13 +332,12 @@ cudaError_t launch_track_step_t(const TrackParams &p, cudaStream_t s) {
   }
   const size_t per_warp = smem_lu_bytes<L>(p.n);
   if (per_warp > kSmemLuMax) {
-    if (sizeof(L) != sizeof(C)) return launch_track_step_t<C, C>(p, s);  // too large to stage: full precision
     const int threads = 128;
     const int64_t blocks = (p.P * 32 + threads - 1) / threads;
-    track_step<C, C, false><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
+    track_step<C, L, false><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
     return cudaGetLastError();
   }
-  const int warps = smem_lu_warps(per_warp);
+  const int warps = kSmemLuWarps;
   const size_t bytes = per_warp * warps;
   if (bytes > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(track_step<C, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -242,6 +242,71 @@ def test_qd_config2_sampled():
     check_exact(s, pts, f, J, points_idx=[0, 511, 1023], polys=[0, 13, 31])
 
 
+def test_qd_config3_sampled_and_euler_identity():
+    """n = 64, m = 256, k = 16, 4096 points (config 3) with quad-double data:
+    sampled outputs against the exact oracle; on the homogeneous variant
+    (degree 24) Euler's identity sum_i x_i df/dx_i = 24 f checked exactly at
+    sampled points, within the quad-double tolerance."""
+    from fractions import Fraction
+
+    s, pts = synth.config(3)
+    s, pts = qd_data(471, s, pts)
+    f, J = run_qd(s, pts)
+    check_exact(s, pts, f, J, points_idx=[0, 4095], polys=[0, 63])
+    s, pts = synth.config(3, homogeneous=True)
+    s, pts = qd_data(472, s, pts)
+    f, J = run_qd(s, pts)
+
+    def fr(v):
+        return sum(Fraction(float(x)) for x in v[:4]), sum(Fraction(float(x)) for x in v[4:])
+
+    for q in (0, 4095):
+        for p in (0, 40):
+            lr, li = Fraction(0), Fraction(0)
+            for i in range(s.n_vars):
+                xr, xi = fr(pts[i, q])
+                jr, ji = fr(J[p, i, q])
+                lr += xr * jr - xi * ji
+                li += xr * ji + xi * jr
+            ffr, ffi = fr(f[p, q])
+            res = abs(complex(float(lr - 24 * ffr), float(li - 24 * ffi)))
+            Sf, _ = E.scales_point(s, pts, q, polys=[p])
+            assert res <= 48 * QD_TOL * Sf[p], (q, p, res / Sf[p])
+
+
+def test_qd_config4_ragged_batch_sampled():
+    """The 200 uneven systems of config 4 in one launch, quad-double data:
+    sampled systems and points against the exact oracle."""
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+
+    systems, pts = synth.config(4)
+    rng = np.random.Generator(np.random.PCG64(473))
+    qs = [s.to_qd(474 + i) for i, s in enumerate(systems)]
+    qp = [synth.widen_qd(rng, p) for p in pts]
+    ev = pkg.PolyEvalMany(qs, [p.shape[1] for p in qp], pkg.PE_QD_INT)
+    fs, Js = ev.eval([to_device(p) for p in qp])
+    torch.cuda.synchronize()
+    assert pkg.polyeval_status(ev.handle) == pkg.PE_OK
+    for si in rng.choice(len(systems), size=5, replace=False):
+        P = qp[si].shape[1]
+        if P == 0:
+            continue
+        q = [0, P - 1] if P > 1 else [0]
+        polys = sorted({0, qs[si].n_polys - 1})
+        check_exact(qs[si], qp[si], fs[si].cpu().numpy(), Js[si].cpu().numpy(), points_idx=q, polys=polys)
+
+
+def test_qd_config5_sampled():
+    """n = 128, m = 1024, k = 32 (config 5) at 2048 of its points, quad-double
+    data: a sampled output row against the exact oracle."""
+    s, pts = synth.config(5, n_points=2048)
+    s, pts = qd_data(475, s, pts)
+    f, J = run_qd(s, pts)
+    check_exact(s, pts, f, J, points_idx=[2047], polys=[127])
+
+
 def test_qd_rejects_newton_and_paper_kernels():
     import paper_1201_0499_gb300 as pkg
 
