@@ -56,9 +56,9 @@ struct CDD {
     const dd r = pe::recip(n2);
     return CDD{pe::mul(z.re, r), pe::mul(negate_if(z.im, 0x8000000000000000ULL), r)};
   }
-  __device__ CDD shfl_down(int d) const {
-    return CDD{dd{__shfl_down_sync(kAll, re.h, d), __shfl_down_sync(kAll, re.l, d)},
-               dd{__shfl_down_sync(kAll, im.h, d), __shfl_down_sync(kAll, im.l, d)}};
+  __device__ CDD shfl_xor(unsigned mask, int d) const {
+    return CDD{dd{__shfl_xor_sync(mask, re.h, d), __shfl_xor_sync(mask, re.l, d)},
+               dd{__shfl_xor_sync(mask, im.h, d), __shfl_xor_sync(mask, im.l, d)}};
   }
 };
 
@@ -90,8 +90,8 @@ struct C64 {
     const double r = __ddiv_rn(1.0, __fma_rn(z.re, z.re, __dmul_rn(z.im, z.im)));
     return C64{__dmul_rn(z.re, r), -__dmul_rn(z.im, r)};
   }
-  __device__ C64 shfl_down(int d) const {
-    return C64{__shfl_down_sync(kAll, re, d), __shfl_down_sync(kAll, im, d)};
+  __device__ C64 shfl_xor(unsigned mask, int d) const {
+    return C64{__shfl_xor_sync(mask, re, d), __shfl_xor_sync(mask, im, d)};
   }
 };
 

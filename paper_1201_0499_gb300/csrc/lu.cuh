@@ -1,5 +1,5 @@
 // Solution of one point's linear system J y = b by LU decomposition with
-// partial pivoting, by one warp, in place: either in the structure-of-arrays
+// partial pivoting, by a segment of a warp (or one thread), in place: either in the structure-of-arrays
 // layout the evaluator writes (J [n][n][P], b [n][P], point index fastest;
 // PointView) or in a copy in the warp's shared memory (row-major [n][n] and
 // [n]; SmemView), which turns the chains of dependent global loads and stores
@@ -50,34 +50,68 @@ __host__ __device__ constexpr size_t smem_lu_bytes(int n) {
   return static_cast<size_t>(n) * (n + 1) * C::kDoubles * sizeof(double);
 }
 constexpr size_t kSmemLuMax = 16 * 1024;
-constexpr int kSmemLuWarps = 4;  // warps per block of the shared-memory variant
+constexpr int kLuBlock = 128;  // threads per block of the segment kernels
 
-// Returns true (warp-uniform) when a pivot column is exactly zero; b is then
-// left partly eliminated.
-template <class C, class V>
-__device__ bool lu_solve(const V &v, int lane) {
-  const int n = v.n;
+// The lanes that work on one point: S consecutive lanes of a warp (S a power
+// of two, 4 .. 32) and the mask of their segment.  A warp holds 32 / S points,
+// so that a small system does not leave most lanes idle: on GB300 an FP64
+// warp instruction occupies the FP64 pipe for the same 16 cycles whatever
+// its active lanes.  Shuffles and barriers use the segment's mask, so the
+// points of one warp may take different branches.
+template <int S>
+struct Lanes {
+  static constexpr int size = S;
+  int lane;       // 0 .. S-1
+  unsigned mask;  // the segment's lanes
+  __device__ static Lanes of_thread() {
+    const int t = static_cast<int>(threadIdx.x & 31);
+    const unsigned m = S == 32 ? 0xffffffffu : (((1u << S) - 1u) << (t & ~(S - 1)));
+    return Lanes{t & (S - 1), m};
+  }
+  __device__ double max(double v) const {
+    for (int d = S / 2; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, d));
+    return v;
+  }
+  __device__ void sync() const { __syncwarp(mask); }
+};
+
+// A single thread working on one point alone.
+struct OneThread {
+  static constexpr int size = 1;
+  static constexpr int lane = 0;
+  __device__ double max(double v) const { return v; }
+  __device__ void sync() const {}
+};
+
+// Lanes per point for an n x n system.
+__host__ __device__ constexpr int lanes_for(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32; }
+
+// Returns true (uniform over the segment) when a pivot column is exactly
+// zero; b is then left partly eliminated.
+template <class C, class V, int S>
+__device__ bool lu_solve(const V &v, const Lanes<S> g) {
+  const int n = v.n, lane = g.lane;
   for (int k = 0; k < n; k++) {
     double best = -1.0;
     int piv = n;
-    for (int i = k + lane; i < n; i += 32) {
+    for (int i = k + lane; i < n; i += S) {
       const double m = C::load(v.Jel(i, k)).abs_hi();
       if (m > best) {
         best = m;
         piv = i;
       }
     }
-    for (int d = 16; d > 0; d >>= 1) {
-      const double ob = __shfl_xor_sync(kAll, best, d);
-      const int op = __shfl_xor_sync(kAll, piv, d);
+    for (int d = S / 2; d > 0; d >>= 1) {
+      const double ob = __shfl_xor_sync(g.mask, best, d);
+      const int op = __shfl_xor_sync(g.mask, piv, d);
       if (ob > best || (ob == best && op < piv)) {
         best = ob;
         piv = op;
       }
     }
-    if (!(best > 0.0)) return true;  // warp-uniform
+    if (!(best > 0.0)) return true;  // uniform over the segment
     if (piv != k) {
-      for (int j = k + lane; j < n; j += 32) {
+      for (int j = k + lane; j < n; j += S) {
         const C a = C::load(v.Jel(k, j)), c = C::load(v.Jel(piv, j));
         c.store(v.Jel(k, j));
         a.store(v.Jel(piv, j));
@@ -87,31 +121,31 @@ __device__ bool lu_solve(const V &v, int lane) {
         c.store(v.bel(k));
         a.store(v.bel(piv));
       }
-      __syncwarp();
+      g.sync();
     }
     // multipliers l_i = J[i][k] / J[k][k] and the right-hand side
     const C inv = C::recip(C::load(v.Jel(k, k)));
     const C bk = C::load(v.bel(k));
-    for (int i = k + 1 + lane; i < n; i += 32) {
+    for (int i = k + 1 + lane; i < n; i += S) {
       const C l = C::mul(C::load(v.Jel(i, k)), inv);
       l.store(v.Jel(i, k));
       C::sub_mul(C::load(v.bel(i)), l, bk).store(v.bel(i));
     }
-    __syncwarp();
+    g.sync();
     // trailing update: lanes over the columns j > k
-    for (int j = k + 1 + lane; j < n; j += 32) {
+    for (int j = k + 1 + lane; j < n; j += S) {
       const C u = C::load(v.Jel(k, j));
       for (int i = k + 1; i < n; i++) C::sub_mul(C::load(v.Jel(i, j)), C::load(v.Jel(i, k)), u).store(v.Jel(i, j));
     }
-    __syncwarp();
+    g.sync();
   }
   // back substitution, y overwrites b
   for (int i = n - 1; i >= 0; i--) {
     C s = C::zero();
-    for (int j = i + 1 + lane; j < n; j += 32) s = C::sub_mul(s, C::load(v.Jel(i, j)), C::load(v.bel(j)));
-    for (int d = 16; d > 0; d >>= 1) s = C::add2(s, s.shfl_down(d));
+    for (int j = i + 1 + lane; j < n; j += S) s = C::sub_mul(s, C::load(v.Jel(i, j)), C::load(v.bel(j)));
+    for (int d = S / 2; d > 0; d >>= 1) s = C::add2(s, s.shfl_xor(g.mask, d));
     if (lane == 0) C::mul(C::add2(C::load(v.bel(i)), s).finish(), C::recip(C::load(v.Jel(i, i)))).store(v.bel(i));
-    __syncwarp();
+    g.sync();
   }
   return false;
 }

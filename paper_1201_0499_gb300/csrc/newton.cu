@@ -3,9 +3,9 @@
 // solve J(x) dx = -f(x) by LU decomposition with partial pivoting, then
 // x <- x + dx.
 //
-// One warp per point (or, for n <= 16, one thread per point) factors the
-// Jacobian the evaluator wrote ([N][n][P], point index fastest) in place
-// (lu.cuh).  Arithmetic in the precision of the
+// A segment of a warp per point (4 to 32 lanes as n needs), or one thread per
+// point for large batches of small systems, factors the Jacobian the
+// evaluator wrote ([N][n][P], point index fastest) in place (lu.cuh).  Arithmetic in the precision of the
 // evaluation (complex double-double, or complex double).  Right-hand side and
 // solution overwrite f.
 #include <cuda_runtime.h>
@@ -21,46 +21,47 @@
 namespace pe {
 
 
-template <class C, bool kSmem>
+template <class C, bool kSmem, int S>
 __global__ void newton_lu(const NewtonParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31;
-  const int64_t q = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;  // one warp per point
-  if (q >= p.P) return;  // warp-uniform
+  const int64_t q = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / S;  // S lanes per point
+  if (q >= p.P) return;  // uniform over the segment
+  const Lanes<S> g = Lanes<S>::of_thread();
+  const int lane = g.lane;
   const int n = p.n;
-  const PointView<C> g{p.J, p.f, n, static_cast<size_t>(p.P), q};
-  double *sm = reinterpret_cast<double *>(smem_raw) + (threadIdx.x >> 5) * (smem_lu_bytes<C>(n) / sizeof(double));
+  const PointView<C> gv{p.J, p.f, n, static_cast<size_t>(p.P), q};
+  double *sm = reinterpret_cast<double *>(smem_raw) + (threadIdx.x / S) * (smem_lu_bytes<C>(n) / sizeof(double));
   const SmemView<C> sv{sm, sm + static_cast<size_t>(n) * n * C::kDoubles, n};
-  auto bel = [&](int i) { return kSmem ? sv.bel(i) : g.bel(i); };
+  auto bel = [&](int i) { return kSmem ? sv.bel(i) : gv.bel(i); };
   auto Xel = [&](int i) { return p.x + (static_cast<size_t>(i) * p.P + q) * C::kDoubles; };
 
   // residual norm; right-hand side b = -f
   double fnorm = 0.0;
-  for (int i = lane; i < n; i += 32) {
-    const C fi = C::load(g.bel(i));
+  for (int i = lane; i < n; i += S) {
+    const C fi = C::load(gv.bel(i));
     fnorm = fmax(fnorm, fi.abs_hi());
     fi.neg().store(bel(i));
   }
-  for (int d = 16; d > 0; d >>= 1) fnorm = fmax(fnorm, __shfl_xor_sync(kAll, fnorm, d));
+  fnorm = g.max(fnorm);
   if (kSmem)
-    for (int e = lane; e < n * n; e += 32) C::load(g.Jel(e / n, e % n)).store(sv.Jel(e / n, e % n));
-  __syncwarp();
+    for (int e = lane; e < n * n; e += S) C::load(gv.Jel(e / n, e % n)).store(sv.Jel(e / n, e % n));
+  g.sync();
 
-  const bool singular = kSmem ? lu_solve<C>(sv, lane) : lu_solve<C>(g, lane);
+  const bool singular = kSmem ? lu_solve<C>(sv, g) : lu_solve<C>(gv, g);
   if (kSmem)  // the factors back to J
-    for (int e = lane; e < n * n; e += 32) C::load(sv.Jel(e / n, e % n)).store(g.Jel(e / n, e % n));
+    for (int e = lane; e < n * n; e += S) C::load(sv.Jel(e / n, e % n)).store(gv.Jel(e / n, e % n));
   double dxnorm = 0.0;
   if (!singular) {
     // x <- x + dx; dx to f
-    for (int i = lane; i < n; i += 32) {
+    for (int i = lane; i < n; i += S) {
       const C dx = C::load(bel(i));
       dxnorm = fmax(dxnorm, dx.abs_hi());
-      dx.store(g.bel(i));
+      dx.store(gv.bel(i));
       C::add2(C::load(Xel(i)), dx).finish().store(Xel(i));
     }
-    for (int d = 16; d > 0; d >>= 1) dxnorm = fmax(dxnorm, __shfl_xor_sync(kAll, dxnorm, d));
+    dxnorm = g.max(dxnorm);
   } else {
-    for (int i = lane; i < n; i += 32) C::zero().store(g.bel(i));
+    for (int i = lane; i < n; i += S) C::zero().store(gv.bel(i));
   }
   if (lane == 0 && p.norms) {
     p.norms[q * 2] = fnorm;
@@ -99,6 +100,24 @@ __global__ void newton_lu_thread(const NewtonParams p) {
   }
 }
 
+template <class C, int S>
+cudaError_t launch_newton_segments(const NewtonParams &p, cudaStream_t s) {
+  const int64_t blocks = (p.P * S + kLuBlock - 1) / kLuBlock;
+  const size_t per_point = smem_lu_bytes<C>(p.n);
+  if (per_point > kSmemLuMax) {
+    newton_lu<C, false, S><<<static_cast<unsigned>(blocks), kLuBlock, 0, s>>>(p);
+    return cudaGetLastError();
+  }
+  const size_t bytes = per_point * (kLuBlock / S);
+  if (bytes > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(newton_lu<C, true, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+    if (e != cudaSuccess) return e;
+  }
+  newton_lu<C, true, S><<<static_cast<unsigned>(blocks), kLuBlock, bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
 template <class C>
 cudaError_t launch_newton_t(const NewtonParams &p, cudaStream_t s) {
   if (thread_lu(p.n, p.P)) {
@@ -106,23 +125,12 @@ cudaError_t launch_newton_t(const NewtonParams &p, cudaStream_t s) {
     newton_lu_thread<C><<<static_cast<unsigned>((p.P + threads - 1) / threads), threads, 0, s>>>(p);
     return cudaGetLastError();
   }
-  const size_t per_warp = smem_lu_bytes<C>(p.n);
-  if (per_warp > kSmemLuMax) {
-    const int threads = 128;
-    const int64_t blocks = (p.P * 32 + threads - 1) / threads;
-    newton_lu<C, false><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
-    return cudaGetLastError();
+  switch (lanes_for(p.n)) {
+    case 4: return launch_newton_segments<C, 4>(p, s);
+    case 8: return launch_newton_segments<C, 8>(p, s);
+    case 16: return launch_newton_segments<C, 16>(p, s);
+    default: return launch_newton_segments<C, 32>(p, s);
   }
-  const int warps = kSmemLuWarps;
-  const size_t bytes = per_warp * warps;
-  if (bytes > 48 * 1024) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(newton_lu<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
-    if (e != cudaSuccess) return e;
-  }
-  const int64_t blocks = (p.P + warps - 1) / warps;
-  newton_lu<C, true><<<static_cast<unsigned>(blocks), warps * 32, bytes, s>>>(p);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_newton(bool dd, const NewtonParams &p, cudaStream_t s) {

@@ -54,31 +54,13 @@ __device__ __forceinline__ C cpow(C x, int e) {  // x^e for e >= 0, by squaring
   return r;
 }
 
-__device__ __forceinline__ double warp_max(double v) {
-  for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(kAll, v, d));
-  return v;
-}
 
 }  // namespace
 
-// The threads that advance one path: a whole warp (lanes split the columns
-// and rows, warp-wide maxima) or a single thread (small n; lu.cuh).
-struct WarpGroup {
-  int lane;
-  static constexpr int size = 32;
-  __device__ double max(double v) const { return warp_max(v); }
-  __device__ void sync() const { __syncwarp(); }
-};
-struct ThreadGroup {
-  static constexpr int lane = 0;
-  static constexpr int size = 1;
-  __device__ double max(double v) const { return v; }
-  __device__ void sync() const {}
-};
-
-// One step of path q.  C: the tracker's arithmetic; L: that of the linear
-// solve (C, or C64 for mixed precision).  kSmem (warp groups only): the
-// system is staged in the warp's shared memory; else a warp forms it in the
+// One step of path q by the group grp (a segment of S lanes, Lanes<S>, or one
+// thread, OneThread).  C: the tracker's arithmetic; L: that of the linear
+// solve (C, or C64 for mixed precision).  kSmem (segments only): the system
+// is staged in the segment's shared memory; else a segment forms it in the
 // evaluator's J and f (L == C) or in the scratch p.JL, p.bL (L != C), and a
 // single thread in place in J and f (as L at the start of each slot).
 template <class C, class L, bool kSmem, class G>
@@ -130,9 +112,9 @@ __device__ void track_path(const TrackParams &p, int64_t q, const G grp, double 
   if constexpr (G::size == 1)
     singular = lu_solve_thread<L>(g);
   else if constexpr (kSmem)
-    singular = lu_solve<L>(sv, lane);
+    singular = lu_solve<L>(sv, grp);
   else
-    singular = lu_solve<L>(gl, lane);
+    singular = lu_solve<L>(gl, grp);
 
   auto restore = [&]() {  // x <- last accepted point
     for (int i = lane; i < n; i += G::size) C::load(Xel(p.xs, i)).store(Xel(p.x, i));
@@ -201,22 +183,22 @@ __device__ void track_path(const TrackParams &p, int64_t q, const G grp, double 
   }
 }
 
-// One warp per path.
-template <class C, class L, bool kSmem>
+// S lanes per path (32 / S paths per warp).
+template <class C, class L, bool kSmem, int S>
 __global__ void track_step(const TrackParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int64_t q = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if (q >= p.P) return;  // warp-uniform
-  double *sm = reinterpret_cast<double *>(smem_raw) + (threadIdx.x >> 5) * (smem_lu_bytes<L>(p.n) / sizeof(double));
-  track_path<C, L, kSmem>(p, q, WarpGroup{static_cast<int>(threadIdx.x & 31)}, sm);
+  const int64_t q = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / S;
+  if (q >= p.P) return;  // uniform over the segment
+  double *sm = reinterpret_cast<double *>(smem_raw) + (threadIdx.x / S) * (smem_lu_bytes<L>(p.n) / sizeof(double));
+  track_path<C, L, kSmem>(p, q, Lanes<S>::of_thread(), sm);
 }
 
-// One thread per path (n <= kThreadLuMaxN).
+// One thread per path (n <= kThreadLuMaxN, large batches).
 template <class C, class L>
 __global__ void track_step_thread(const TrackParams p) {
   const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= p.P) return;
-  track_path<C, L, false>(p, q, ThreadGroup{}, nullptr);
+  track_path<C, L, false>(p, q, OneThread{}, nullptr);
 }
 
 __global__ void track_init(const TrackParams p, double h_init, int words) {
@@ -323,6 +305,24 @@ cudaError_t launch_track_init(bool dd, const TrackParams &p, double h_init, cuda
   return cudaGetLastError();
 }
 
+template <class C, class L, int S>
+cudaError_t launch_track_segments(const TrackParams &p, cudaStream_t s) {
+  const int64_t blocks = (p.P * S + kLuBlock - 1) / kLuBlock;
+  const size_t per_path = smem_lu_bytes<L>(p.n);
+  if (per_path > kSmemLuMax) {
+    track_step<C, L, false, S><<<static_cast<unsigned>(blocks), kLuBlock, 0, s>>>(p);
+    return cudaGetLastError();
+  }
+  const size_t bytes = per_path * (kLuBlock / S);
+  if (bytes > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(track_step<C, L, true, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(bytes));
+    if (e != cudaSuccess) return e;
+  }
+  track_step<C, L, true, S><<<static_cast<unsigned>(blocks), kLuBlock, bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
 template <class C, class L>
 cudaError_t launch_track_step_t(const TrackParams &p, cudaStream_t s) {
   if (thread_lu(p.n, p.P)) {
@@ -330,23 +330,12 @@ cudaError_t launch_track_step_t(const TrackParams &p, cudaStream_t s) {
     track_step_thread<C, L><<<static_cast<unsigned>((p.P + threads - 1) / threads), threads, 0, s>>>(p);
     return cudaGetLastError();
   }
-  const size_t per_warp = smem_lu_bytes<L>(p.n);
-  if (per_warp > kSmemLuMax) {
-    const int threads = 128;
-    const int64_t blocks = (p.P * 32 + threads - 1) / threads;
-    track_step<C, L, false><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
-    return cudaGetLastError();
+  switch (lanes_for(p.n)) {
+    case 4: return launch_track_segments<C, L, 4>(p, s);
+    case 8: return launch_track_segments<C, L, 8>(p, s);
+    case 16: return launch_track_segments<C, L, 16>(p, s);
+    default: return launch_track_segments<C, L, 32>(p, s);
   }
-  const int warps = kSmemLuWarps;
-  const size_t bytes = per_warp * warps;
-  if (bytes > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(track_step<C, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(bytes));
-    if (e != cudaSuccess) return e;
-  }
-  const int64_t blocks = (p.P + warps - 1) / warps;
-  track_step<C, L, true><<<static_cast<unsigned>(blocks), warps * 32, bytes, s>>>(p);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_track_step(bool dd, const TrackParams &p, cudaStream_t s) {

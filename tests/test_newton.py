@@ -71,8 +71,9 @@ def run_newton(system, pts, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_newton_step_against_exact(prec):
-    n, P = 5, 21
+@pytest.mark.parametrize("n", [5, 12])
+def test_newton_step_against_exact(prec, n):
+    P = 21
     s = square_system(201, n, m=6, kmax=3, emax=3)
     pts = synth.points(202, n, P)
     if prec == "f64":

@@ -129,6 +129,18 @@ def test_track_generic_matches_oracle(prec, case):
         assert exact_residual(s, raw) <= 1e-24
 
 
+@pytest.mark.parametrize("prec", TRACK_PRECS)
+def test_track_nine_variables_sixteen_lane_segments(prec):
+    """n = 9 (16 lanes per path, two paths per warp) against the oracle."""
+    s = synth.dense_system(621, 9, [2, 2, 2, 1, 1, 1, 1, 1, 1])
+    ref = T.solve_system(s.as_fp64() if prec == "f64" else s)
+    z, raw, st, _, _ = run_track(s, prec)
+    assert len(st) == 8 and np.all(st == 1)
+    assert match(list(z), [x for x, _ in ref], 1e-8)
+    if prec != "f64":
+        assert exact_residual(s, raw) <= 1e-24
+
+
 def test_track_start_points_on_device():
     import torch
 
