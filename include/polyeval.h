@@ -407,10 +407,13 @@ PE_API int polyeval_start_points(polyeval_t *h, int64_t first, int64_t P, void *
  *   t, status   device [P] arrays (either may be NULL): the last accepted t
  *               and the PE_PATH_* status of each path
  *   iterations  host, or NULL: iterations the batch took
- * Blocks the calling thread: it synchronises `stream` every 8 iterations to
- * read how many paths still run, and returns when none does (or after
- * max_iters).  Allocates the tracker's scratch on the handle on first use
- * (F, J_F, saved points, path states for P paths).  Not for stream capture.
+ * Blocks the calling thread: it synchronises `stream` (so that the start
+ * points are in place), then runs the iterations on a stream of the
+ * handle's own, replaying batches of 8 iterations from a CUDA graph captured
+ * on the first call, reads how many paths still run after each batch, and
+ * returns when none does (or after max_iters) with all its work complete.
+ * Allocates the tracker's scratch and stream on the handle on first use (F,
+ * J_F, saved points, path states for P paths).  Not for stream capture.
  * Errors: PE_EINVAL (as polyeval_start_points, bad parameters), PE_ERANGE
  * (P > max_points), PE_ENOMEM, PE_ECUDA.
  */

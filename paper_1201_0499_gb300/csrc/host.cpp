@@ -92,6 +92,7 @@ struct polyeval {
   // the tracker's scratch, allocated on first use
   std::vector<int32_t> degrees;
   DeviceBuf deg_dev, tr_f, tr_J, tr_xs, tr_state, tr_active, tr_x64, tr_status, tr_xc, tr_statc, tr_idx, tr_JL, tr_bL;
+  cudaStream_t tr_stream = nullptr;  // the tracker's own stream (graph capture needs one)
   struct Tuned {
     int64_t P;
     int chunks;
@@ -106,6 +107,7 @@ struct polyeval {
   ~polyeval() {
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
+    if (tr_stream) cudaStreamDestroy(tr_stream);
   }
 };
 
@@ -1059,6 +1061,8 @@ bool params_ok(const pe_track_params *p) {
          (p->gamma_re != 0.0 || p->gamma_im != 0.0);
 }
 
+constexpr int kGraphIters = 8;  // tracker iterations per captured graph
+
 int track(polyeval *h, const pe_track_params *prm, double *x, int64_t P, double *t_out, int32_t *status,
           int64_t *iterations, cudaStream_t s) {
   if (iterations) *iterations = 0;
@@ -1093,24 +1097,71 @@ int track(polyeval *h, const pe_track_params *prm, double *x, int64_t P, double 
     tp.bL = static_cast<double *>(h->tr_bL.p);
   }
   tp.active = static_cast<unsigned *>(h->tr_active.p);
-  if (pe::launch_track_init(h->dd, tp, prm->h_init, s) != cudaSuccess) return PE_ECUDA;
-  int64_t it = 0;
-  unsigned running = 1;
-  while (it < prm->max_iters && running) {
-    if (cudaMemsetAsync(tp.active, 0, sizeof(unsigned), s) != cudaSuccess) return PE_ECUDA;
-    if ((rc = polyeval_eval(h, x, P, tp.f, tp.J, s)) != PE_OK) return rc;
-    if (pe::launch_track_step(h->dd, tp, s) != cudaSuccess) return PE_ECUDA;
+  // The iterations run on the handle's own stream: the batch of kGraphIters
+  // iterations (counter reset, evaluation, step) is captured once into a CUDA
+  // graph and replayed, which removes the host overhead of its dozens of
+  // short launches; the running-path count is read after each replay.
+  if (!h->tr_stream && cudaStreamCreateWithFlags(&h->tr_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    h->tr_stream = nullptr;
+    return PE_ECUDA;
+  }
+  cudaStream_t ts = h->tr_stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PE_ECUDA;  // start points queued by the caller
+  if (pe::launch_track_init(h->dd, tp, prm->h_init, ts) != cudaSuccess) return PE_ECUDA;
+  const bool timing = h->timing;
+  h->timing = false;  // no event pairs inside the graph
+  auto iteration = [&](cudaStream_t st) -> int {
+    if (cudaMemsetAsync(tp.active, 0, sizeof(unsigned), st) != cudaSuccess) return PE_ECUDA;
+    int r = polyeval_eval(h, x, P, tp.f, tp.J, st);
+    if (r != PE_OK) return r;
+    if (pe::launch_track_step(h->dd, tp, st) != cudaSuccess) return PE_ECUDA;
     h->kernels_launched++;
-    it++;
-    if ((it & 7) == 0 || it == prm->max_iters) {
-      if (cudaMemcpyAsync(&running, tp.active, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess)
-        return PE_ECUDA;
+    return PE_OK;
+  };
+  struct Graph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t e = nullptr;
+    ~Graph() {
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
+    }
+  } graph;
+  int64_t per_replay = 0;
+  if (prm->max_iters >= kGraphIters) {
+    const int64_t k0 = h->kernels_launched;
+    if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = PE_ECUDA;
+    for (int i = 0; i < kGraphIters && rc == PE_OK; i++) rc = iteration(ts);
+    const cudaError_t ce = cudaStreamEndCapture(ts, &graph.g);  // always leave capture mode
+    if (rc == PE_OK && (ce != cudaSuccess || cudaGraphInstantiate(&graph.e, graph.g, 0) != cudaSuccess)) rc = PE_ECUDA;
+    per_replay = h->kernels_launched - k0;
+    h->kernels_launched = k0;
+    if (rc != PE_OK) {
+      cudaGetLastError();
+      h->timing = timing;
+      return rc;
     }
   }
-  if (pe::launch_track_finish(tp.st, P, t_out, status, s) != cudaSuccess) return PE_ECUDA;
+  int64_t it = 0;
+  unsigned running = 1;
+  while (it < prm->max_iters && running && rc == PE_OK) {
+    if (graph.e && it + kGraphIters <= prm->max_iters) {
+      if (cudaGraphLaunch(graph.e, ts) != cudaSuccess) rc = PE_ECUDA;
+      h->kernels_launched += per_replay;
+      it += kGraphIters;
+    } else {
+      rc = iteration(ts);
+      it++;
+    }
+    if (rc == PE_OK && (cudaMemcpyAsync(&running, tp.active, sizeof(unsigned), cudaMemcpyDeviceToHost, ts) !=
+                            cudaSuccess ||
+                        cudaStreamSynchronize(ts) != cudaSuccess))
+      rc = PE_ECUDA;
+  }
+  h->timing = timing;
+  if (rc != PE_OK) return rc;
+  if (pe::launch_track_finish(tp.st, P, t_out, status, ts) != cudaSuccess) return PE_ECUDA;
   if (iterations) *iterations = it;
-  return cudaStreamSynchronize(s) == cudaSuccess ? PE_OK : PE_ECUDA;
+  return cudaStreamSynchronize(ts) == cudaSuccess ? PE_OK : PE_ECUDA;
 }
 
 }  // namespace

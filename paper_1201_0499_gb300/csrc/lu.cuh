@@ -1,16 +1,19 @@
 // Solution of one point's linear system J y = b by LU decomposition with
-// partial pivoting, by a segment of a warp (or one thread), in place: either in the structure-of-arrays
-// layout the evaluator writes (J [n][n][P], b [n][P], point index fastest;
-// PointView) or in a copy in the warp's shared memory (row-major [n][n] and
-// [n]; SmemView), which turns the chains of dependent global loads and stores
-// of the elimination into shared-memory accesses.  Used by the Newton step
-// (newton.cu) and the path tracker (track.cu).
+// partial pivoting, by a segment of a warp, in place: either in the
+// structure-of-arrays layout the evaluator writes (J [n][n][P], b [n][P],
+// point index fastest; PointView) or in a copy in shared memory (row-major
+// [n][n] and [n]; SmemView), which turns the chains of dependent global loads
+// and stores of the elimination into shared-memory accesses.  Used by the
+// Newton step (newton.cu) and the path tracker (track.cu).
 //
-// In elimination step k the lanes take the columns j > k of the trailing
-// rows (lane j, j + 32, ...), the pivot is the row of largest |J[i][k]| (by
-// the leading parts; the smallest index on ties) found by a warp-wide
-// arg-max, the multipliers are formed by the lanes that own their rows, and
-// the back substitution reduces each row's dot product across the warp.
+// In elimination step k the lanes of the segment take the columns j > k of
+// the trailing rows (lane j, j + S, ...), the pivot is the row of largest
+// |J[i][k]| (by the leading parts; the smallest index on ties) found by a
+// segment-wide arg-max, the multipliers are formed by the lanes that own their
+// rows, and the back substitution reduces each row's dot product across the
+// segment.  (One thread per point, each running a whole elimination, was
+// slower at every batch size measured, up to 16384 points of 14 variables:
+// its dependent chains of loads and stores leave the SMs waiting.)
 // On return J holds the factors (unit lower triangle below the diagonal,
 // after the row exchanges) and b the solution y.
 #pragma once
@@ -73,14 +76,6 @@ struct Lanes {
     return v;
   }
   __device__ void sync() const { __syncwarp(mask); }
-};
-
-// A single thread working on one point alone.
-struct OneThread {
-  static constexpr int size = 1;
-  static constexpr int lane = 0;
-  __device__ double max(double v) const { return v; }
-  __device__ void sync() const {}
 };
 
 // Lanes per point for an n x n system.
@@ -146,63 +141,6 @@ __device__ bool lu_solve(const V &v, const Lanes<S> g) {
     for (int d = S / 2; d > 0; d >>= 1) s = C::add2(s, s.shfl_xor(g.mask, d));
     if (lane == 0) C::mul(C::add2(C::load(v.bel(i)), s).finish(), C::recip(C::load(v.Jel(i, i)))).store(v.bel(i));
     g.sync();
-  }
-  return false;
-}
-
-// One thread per point, for small n: the whole elimination by the thread that
-// owns the point, on its own elements of the [.][P] layout (a warp's 32
-// threads touch 32 consecutive points of every element, so each access is
-// coalesced and every lane does useful arithmetic -- the warp-per-point
-// version leaves 32 - n lanes idle, and on GB300 an FP64 warp instruction
-// costs the FP64 pipe the same whatever its active lanes).  Elements are
-// read and written as L at the start of each slot of the view (L may be
-// narrower than the view's element).  Full rows are exchanged.  A thread's
-// elimination is a long dependent chain, so this pays only when enough
-// points run at once to keep every SM's FP64 pipe busy: n <= kThreadLuMaxN
-// and at least kThreadLuMinP points (below that the warp-per-point solve,
-// which spreads each point over n lanes, finishes first).
-constexpr int kThreadLuMaxN = 16;
-constexpr int64_t kThreadLuMinP = 4096;
-inline bool thread_lu(int n, int64_t P) { return n <= kThreadLuMaxN && P >= kThreadLuMinP; }
-
-template <class L, class V>
-__device__ bool lu_solve_thread(const V &v) {
-  const int n = v.n;
-  for (int k = 0; k < n; k++) {
-    double best = -1.0;
-    int piv = k;
-    for (int i = k; i < n; i++) {
-      const double m = L::load(v.Jel(i, k)).abs_hi();
-      if (m > best) {
-        best = m;
-        piv = i;
-      }
-    }
-    if (!(best > 0.0)) return true;
-    if (piv != k) {
-      for (int j = 0; j < n; j++) {
-        const L a = L::load(v.Jel(k, j)), c = L::load(v.Jel(piv, j));
-        c.store(v.Jel(k, j));
-        a.store(v.Jel(piv, j));
-      }
-      const L a = L::load(v.bel(k)), c = L::load(v.bel(piv));
-      c.store(v.bel(k));
-      a.store(v.bel(piv));
-    }
-    const L inv = L::recip(L::load(v.Jel(k, k)));
-    const L bk = L::load(v.bel(k));
-    for (int i = k + 1; i < n; i++) {
-      const L l = L::mul(L::load(v.Jel(i, k)), inv);
-      l.store(v.Jel(i, k));
-      L::sub_mul(L::load(v.bel(i)), l, bk).store(v.bel(i));
-      for (int j = k + 1; j < n; j++) L::sub_mul(L::load(v.Jel(i, j)), l, L::load(v.Jel(k, j))).store(v.Jel(i, j));
-    }
-  }
-  for (int i = n - 1; i >= 0; i--) {
-    L s = L::load(v.bel(i));
-    for (int j = i + 1; j < n; j++) s = L::sub_mul(s, L::load(v.Jel(i, j)), L::load(v.bel(j)));
-    L::mul(s.finish(), L::recip(L::load(v.Jel(i, i)))).store(v.bel(i));
   }
   return false;
 }

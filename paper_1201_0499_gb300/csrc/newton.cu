@@ -3,9 +3,9 @@
 // solve J(x) dx = -f(x) by LU decomposition with partial pivoting, then
 // x <- x + dx.
 //
-// A segment of a warp per point (4 to 32 lanes as n needs), or one thread per
-// point for large batches of small systems, factors the Jacobian the
-// evaluator wrote ([N][n][P], point index fastest) in place (lu.cuh).  Arithmetic in the precision of the
+// A segment of a warp per point (4 to 32 lanes as n needs) factors the
+// Jacobian the evaluator wrote ([N][n][P], point index fastest) in place
+// (lu.cuh).  Arithmetic in the precision of the
 // evaluation (complex double-double, or complex double).  Right-hand side and
 // solution overwrite f.
 #include <cuda_runtime.h>
@@ -69,37 +69,6 @@ __global__ void newton_lu(const NewtonParams p) {
   }
 }
 
-// One thread per point (n <= kThreadLuMaxN).
-template <class C>
-__global__ void newton_lu_thread(const NewtonParams p) {
-  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (q >= p.P) return;
-  const int n = p.n;
-  const PointView<C> g{p.J, p.f, n, static_cast<size_t>(p.P), q};
-  auto Xel = [&](int i) { return p.x + (static_cast<size_t>(i) * p.P + q) * C::kDoubles; };
-  double fnorm = 0.0;
-  for (int i = 0; i < n; i++) {
-    const C fi = C::load(g.bel(i));
-    fnorm = fmax(fnorm, fi.abs_hi());
-    fi.neg().store(g.bel(i));
-  }
-  const bool singular = lu_solve_thread<C>(g);
-  double dxnorm = 0.0;
-  for (int i = 0; i < n; i++) {
-    if (singular) {
-      C::zero().store(g.bel(i));
-    } else {
-      const C dx = C::load(g.bel(i));
-      dxnorm = fmax(dxnorm, dx.abs_hi());
-      C::add2(C::load(Xel(i)), dx).finish().store(Xel(i));
-    }
-  }
-  if (p.norms) {
-    p.norms[q * 2] = fnorm;
-    p.norms[q * 2 + 1] = singular ? nan("") : dxnorm;
-  }
-}
-
 template <class C, int S>
 cudaError_t launch_newton_segments(const NewtonParams &p, cudaStream_t s) {
   const int64_t blocks = (p.P * S + kLuBlock - 1) / kLuBlock;
@@ -120,11 +89,6 @@ cudaError_t launch_newton_segments(const NewtonParams &p, cudaStream_t s) {
 
 template <class C>
 cudaError_t launch_newton_t(const NewtonParams &p, cudaStream_t s) {
-  if (thread_lu(p.n, p.P)) {
-    const int threads = 32;
-    newton_lu_thread<C><<<static_cast<unsigned>((p.P + threads - 1) / threads), threads, 0, s>>>(p);
-    return cudaGetLastError();
-  }
   switch (lanes_for(p.n)) {
     case 4: return launch_newton_segments<C, 4>(p, s);
     case 8: return launch_newton_segments<C, 8>(p, s);

@@ -25,7 +25,7 @@
 // Mixed precision (double-double tracking with `mixed` set): the homotopy,
 // the right-hand sides and the points stay in double-double, the linear
 // systems are solved in double from the leading parts of H_x (in shared
-// memory, in the tracker's double scratch, or in place per thread).  Each corrector step is then a step of iterative
+// memory or in the tracker's double scratch).  Each corrector step is then a step of iterative
 // refinement, whose error falls by about u cond(H_x) (u = 2^-53) per step, and
 // the step kernel runs about a tenth of the FP64 instructions of a
 // double-double LU -- on GB300, whose FP64 pipe issues a warp instruction in
@@ -57,12 +57,10 @@ __device__ __forceinline__ C cpow(C x, int e) {  // x^e for e >= 0, by squaring
 
 }  // namespace
 
-// One step of path q by the group grp (a segment of S lanes, Lanes<S>, or one
-// thread, OneThread).  C: the tracker's arithmetic; L: that of the linear
-// solve (C, or C64 for mixed precision).  kSmem (segments only): the system
-// is staged in the segment's shared memory; else a segment forms it in the
-// evaluator's J and f (L == C) or in the scratch p.JL, p.bL (L != C), and a
-// single thread in place in J and f (as L at the start of each slot).
+// One step of path q by the S lanes of grp.  C: the tracker's arithmetic; L:
+// that of the linear solve (C, or C64 for mixed precision).  kSmem: the
+// system is staged in the segment's shared memory; else it is formed in the
+// evaluator's J and f (L == C) or in the scratch p.JL, p.bL (L != C).
 template <class C, class L, bool kSmem, class G>
 __device__ void track_path(const TrackParams &p, int64_t q, const G grp, double *sm) {
   TrackState s = p.st[q];
@@ -71,11 +69,11 @@ __device__ void track_path(const TrackParams &p, int64_t q, const G grp, double 
   const size_t P = static_cast<size_t>(p.P);
   const PointView<C> g{p.J, p.f, n, P, q};
   const SmemView<L> sv{sm, sm + static_cast<size_t>(n) * n * L::kDoubles, n};
-  // a warp's in-place system: the evaluator's arrays, or the double scratch
-  constexpr bool kScratch = G::size > 1 && !kSmem && sizeof(L) != sizeof(C);
+  // the in-place system: the evaluator's arrays, or the double scratch
+  constexpr bool kScratch = !kSmem && sizeof(L) != sizeof(C);
   const PointView<L> gl{kScratch ? p.JL : p.J, kScratch ? p.bL : p.f, n, P, q};
-  auto Ael = [&](int i, int j) { return kSmem ? sv.Jel(i, j) : G::size > 1 ? gl.Jel(i, j) : g.Jel(i, j); };
-  auto bel = [&](int i) { return kSmem ? sv.bel(i) : G::size > 1 ? gl.bel(i) : g.bel(i); };
+  auto Ael = [&](int i, int j) { return kSmem ? sv.Jel(i, j) : gl.Jel(i, j); };
+  auto bel = [&](int i) { return kSmem ? sv.bel(i) : gl.bel(i); };
   auto Xel = [&](double *base, int i) { return base + (static_cast<size_t>(i) * P + q) * C::kDoubles; };
   const C gamma = C::make(p.gre, p.gim);
 
@@ -109,9 +107,7 @@ __device__ void track_path(const TrackParams &p, int64_t q, const G grp, double 
   grp.sync();
 
   bool singular;
-  if constexpr (G::size == 1)
-    singular = lu_solve_thread<L>(g);
-  else if constexpr (kSmem)
+  if constexpr (kSmem)
     singular = lu_solve<L>(sv, grp);
   else
     singular = lu_solve<L>(gl, grp);
@@ -191,14 +187,6 @@ __global__ void track_step(const TrackParams p) {
   if (q >= p.P) return;  // uniform over the segment
   double *sm = reinterpret_cast<double *>(smem_raw) + (threadIdx.x / S) * (smem_lu_bytes<L>(p.n) / sizeof(double));
   track_path<C, L, kSmem>(p, q, Lanes<S>::of_thread(), sm);
-}
-
-// One thread per path (n <= kThreadLuMaxN, large batches).
-template <class C, class L>
-__global__ void track_step_thread(const TrackParams p) {
-  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (q >= p.P) return;
-  track_path<C, L, false>(p, q, OneThread{}, nullptr);
 }
 
 __global__ void track_init(const TrackParams p, double h_init, int words) {
@@ -325,11 +313,6 @@ cudaError_t launch_track_segments(const TrackParams &p, cudaStream_t s) {
 
 template <class C, class L>
 cudaError_t launch_track_step_t(const TrackParams &p, cudaStream_t s) {
-  if (thread_lu(p.n, p.P)) {
-    const int threads = 32;
-    track_step_thread<C, L><<<static_cast<unsigned>((p.P + threads - 1) / threads), threads, 0, s>>>(p);
-    return cudaGetLastError();
-  }
   switch (lanes_for(p.n)) {
     case 4: return launch_track_segments<C, L, 4>(p, s);
     case 8: return launch_track_segments<C, L, 8>(p, s);

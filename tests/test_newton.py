@@ -163,8 +163,9 @@ def test_newton_converges_on_the_benchmark_system(prec):
 
 @pytest.mark.parametrize("prec", ["dd", "f64"])
 def test_newton_large_batch_small_system(prec):
-    """4096 points of an 8 x 8 system: the one-thread-per-point solve.  The
-    step is checked against the exact Newton step at sampled points."""
+    """4096 points of an 8 x 8 system (8-lane segments, four points per
+    warp).  The step is checked against the exact Newton step at sampled
+    points."""
     n, P = 8, 4096
     s = square_system(205, n, m=5, kmax=3, emax=3)
     pts = synth.points(206, n, P)

@@ -243,10 +243,10 @@ def test_track_large_system_two_paths(mixed):
 
 
 @pytest.mark.parametrize("prec", ["f64", "dd"])
-def test_track_large_batch_thread_per_path(prec):
-    """4096 paths (twelve quadrics): the batch is large enough for the
-    one-thread-per-path linear solves.  Every path succeeds at a distinct end
-    point; sampled end points have tiny exact residuals."""
+def test_track_large_batch(prec):
+    """4096 paths (twelve quadrics, 16-lane segments, two paths per warp).
+    Every path succeeds at a distinct end point; sampled end points have tiny
+    exact residuals."""
     s = synth.dense_system(620, 12, [2] * 12)
     z, raw, st, _, _ = run_track(s, prec)
     assert len(st) == 4096 and np.all(st == 1)
