@@ -18,7 +18,9 @@
  *   - Return value: PE_OK (0) or a negative PE_E* code; nothing aborts and no
  *     C++ exception crosses this interface.  polyeval_strerror() names codes.
  *   - "device" pointers are CUDA global-memory addresses on the current
- *     device; "host" pointers are ordinary CPU memory.
+ *     device; "host" pointers are ordinary CPU memory.  Device arrays of
+ *     points, coefficients and outputs must be 16-byte aligned (cudaMalloc
+ *     and torch allocations are); a misaligned one is PE_EINVAL.
  *   - Streams are passed as `void *` holding a cudaStream_t (NULL = legacy
  *     default stream).  Every eval call is asynchronous on that stream.
  *   - All sizes are element counts unless stated.

@@ -115,6 +115,12 @@ namespace {
 
 int elem_doubles(const polyeval *h) { return h->qd ? 8 : h->dd ? 4 : 2; }
 
+// Device arrays are read and written with 16-byte vector accesses.
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool arrays_aligned(const void *a, const void *b, const void *c) {
+  return aligned16(a) && aligned16(b) && aligned16(c);
+}
+
 // Products on the integer pipes (block-format table and coefficients).
 bool block_format(const polyeval *h) { return h->wide || h->qd; }
 
@@ -714,6 +720,7 @@ int eval_single(polyeval *h, const void *points, int64_t P, void *out_f, void *o
   if (P == 0) return PE_OK;
   if (P > h->max_points) return PE_ERANGE;
   if (!points || (!out_f && h->sys[0].N > 0) || (!out_J && h->sys[0].N > 0)) return PE_EINVAL;
+  if (!arrays_aligned(points, out_f, out_J)) return PE_EINVAL;
   const SysDesc &d = h->sys[0];
   if (h->paper) {
     pe::PaperParams pp{};
@@ -896,7 +903,7 @@ int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, void *o
 int polyeval_eval_many(polyeval_t *h, const void *points, void *out_f, void *out_J, void *stream) {
   if (!h || !h->batch) return PE_EINVAL;
   if (h->n_items_batch == 0) return PE_OK;
-  if (!points || !out_f || !out_J) return PE_EINVAL;
+  if (!points || !out_f || !out_J || !arrays_aligned(points, out_f, out_J)) return PE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (h->power_total_batch > 0) {
     pe::PowerParams pp{};
@@ -1201,7 +1208,7 @@ int polyeval_bezout(const polyeval_t *h, double *count, int32_t *degrees) {
 int polyeval_start_points(polyeval_t *h, int64_t first, int64_t P, void *points, void *stream) {
   if (!trackable(h) || first < 0 || P < 0) return PE_EINVAL;
   if (P == 0) return PE_OK;
-  if (!points) return PE_EINVAL;
+  if (!points || !aligned16(points)) return PE_EINVAL;
   int rc;
   if ((rc = upload_degrees(h)) != PE_OK) return rc;
   return pe::launch_start_points(h->dd, h->sys[0].n, static_cast<const int32_t *>(h->deg_dev.p), first, P,
@@ -1215,7 +1222,7 @@ int polyeval_track(polyeval_t *h, const pe_track_params *prm, void *points, int6
   if (iterations) *iterations = 0;
   if (!trackable(h) || !params_ok(prm) || P < 0) return PE_EINVAL;
   if (P > h->max_points) return PE_ERANGE;
-  if (P > 0 && !points) return PE_EINVAL;
+  if (P > 0 && (!points || !aligned16(points))) return PE_EINVAL;
   return track(h, prm, static_cast<double *>(points), P, t, status, iterations, static_cast<cudaStream_t>(stream));
 }
 
@@ -1229,7 +1236,7 @@ int polyeval_track_adaptive(polyeval_t *h_lo, polyeval_t *h_hi, const pe_track_p
   if (h_lo->sys[0].n != h_hi->sys[0].n || h_lo->degrees != h_hi->degrees) return PE_EINVAL;
   if (P > h_lo->max_points || P > h_hi->max_points) return PE_ERANGE;
   if (P == 0) return PE_OK;
-  if (!points || !status) return PE_EINVAL;
+  if (!points || !status || !aligned16(points)) return PE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int32_t n = h_hi->sys[0].n;
   double *x = static_cast<double *>(points);

@@ -230,6 +230,9 @@ extern "C" PE_API int polyeval_eval_noalloc(const pe_system *dev_sys, int32_t ma
   if (!dev_sys->poly_ptr || !dev_sys->mono_ptr || !dev_sys->pos || !dev_sys->exp || !dev_sys->coef || !points ||
       !out_f || !out_J)
     return PE_EINVAL;
+  // 16-byte vector accesses of points, coefficients and outputs
+  const auto misaligned = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) != 0; };
+  if (misaligned(points) || misaligned(out_f) || misaligned(out_J) || misaligned(dev_sys->coef)) return PE_EINVAL;
   const int64_t table_entries = max_exp > 2 ? static_cast<int64_t>(max_exp - 2) * dev_sys->n_vars * P : 0;
   if (table_entries > static_cast<int64_t>(kNoAllocScratchBytes / (4 * sizeof(double)))) return PE_ERANGE;
   const int64_t T = (P + kTile - 1) / kTile;

@@ -209,6 +209,15 @@ def test_argument_errors():
         pkg.polyeval_create(s, 7, 0, 4)
     with pytest.raises(pkg.PolyEvalError):
         pkg.polyeval_create(s, pkg.PE_DD, 0, 0)
+    # device arrays must be 16-byte aligned (vector accesses): rejected on the host
+    x8 = to_device(synth.points(114, 4, 8))
+    f = torch.empty((2, 8, 4), dtype=torch.float64, device="cuda")
+    J = torch.empty((2, 4, 8, 4), dtype=torch.float64, device="cuda")
+    for args in ((x8.data_ptr() + 8, f.data_ptr(), J.data_ptr()), (x8.data_ptr(), f.data_ptr() + 8, J.data_ptr()),
+                 (x8.data_ptr(), f.data_ptr(), J.data_ptr() + 8)):
+        with pytest.raises(pkg.PolyEvalError) as e:
+            pkg.polyeval_eval(ev.handle, args[0], 7, args[1], args[2])
+        assert e.value.code == pkg.PE_EINVAL
 
 
 def test_deterministic_and_host_entry_point_agree():
