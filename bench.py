@@ -598,7 +598,7 @@ def main():
             "vs_baseline": None,
             "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": wl.text, "points_per_gpu": P,
+            "config": {"workload": wl.text, "points_per_gpu": P, "gpu": torch.cuda.get_device_name(dev),
                        "precision": ("complex double-double" if args.precision == "dd" else
                                      "complex double-double in/out, products in 128-bit integer block floating point"),
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",

@@ -215,6 +215,16 @@ PE_API int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void 
                              int *chunks, int *shape);
 
 /*
+ * Set the launch polyeval_eval uses for calls with exactly P points (what
+ * polyeval_autotune would store): chunks 1..8 monomial chunks per polynomial
+ * (capped by the handle's scratch at run time) and shape 1 (one single-warp
+ * block per work item) or 2 (persistent grid).  0 for either leaves that
+ * choice to the built-in heuristic; chunks = shape = 0 removes the entry.
+ * Single-system handles.  Errors: PE_EINVAL.
+ */
+PE_API int polyeval_set_launch(polyeval_t *h, int64_t P, int chunks, int shape);
+
+/*
  * One Newton step x <- x + dx, J(x) dx = -f(x), at P points of a square
  * system (n_polys == n_vars).  Evaluating f and J is the expensive part of
  * Newton's method, the corrector of a path tracker (Section 1); this entry

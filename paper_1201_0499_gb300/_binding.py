@@ -116,6 +116,7 @@ def load_library(path: Optional[str] = None):
         "polyeval_newton": ([P, P, I64, P, P, P, P], ctypes.c_int),
         "polyeval_autotune": ([P, P, I64, P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                               ctypes.c_int),
+        "polyeval_set_launch": ([P, I64, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "polyeval_track_defaults": ([ctypes.c_int, ctypes.POINTER(pe_track_params)], ctypes.c_int),
         "polyeval_bezout": ([P, D, ctypes.POINTER(I32)], ctypes.c_int),
         "polyeval_start_points": ([P, I64, I64, P, P], ctypes.c_int),
@@ -234,6 +235,11 @@ def polyeval_autotune(h: int, points, P: int, out_f, out_J, stream=None):
     _check(load_library().polyeval_autotune(h, _addr(points), int(P), _addr(out_f), _addr(out_J), _stream(stream),
                                             ctypes.byref(c), ctypes.byref(m)), "polyeval_autotune")
     return c.value, m.value
+
+
+def polyeval_set_launch(h: int, P: int, chunks: int = 0, shape: int = 0) -> None:
+    """Fix the launch for calls with P points (0 = built-in choice)."""
+    _check(load_library().polyeval_set_launch(h, int(P), int(chunks), int(shape)), "polyeval_set_launch")
 
 
 def polyeval_newton(h: int, points, P: int, out_f, out_J, norms=None, stream=None) -> None:

@@ -886,6 +886,17 @@ int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void *out_f,
 }
 
 
+int polyeval_set_launch(polyeval_t *h, int64_t P, int chunks, int shape) {
+  if (!h || h->batch || P < 1 || chunks < 0 || chunks > kMaxChunks || shape < 0 || shape > 2) return PE_EINVAL;
+  for (auto it = h->tuned.begin(); it != h->tuned.end(); ++it)
+    if (it->P == P) {
+      h->tuned.erase(it);
+      break;
+    }
+  if (chunks > 0 || shape > 0) h->tuned.push_back(polyeval::Tuned{P, chunks, shape});
+  return PE_OK;
+}
+
 int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, void *out_J, double *norms, void *stream) {
   if (!h || h->batch || h->qd) return PE_EINVAL;
   const SysDesc &d = h->sys[0];

@@ -471,3 +471,32 @@ def test_autotune_then_eval(prec):
     torch.cuda.synchronize()
     assert ev.status() == pkg.PE_OK
     check_exact_oracle(s, pts, f.cpu().numpy(), J.cpu().numpy(), DD_TOL, points_idx=[0, 299], polys=[0, 31])
+
+
+@pytest.mark.parametrize("prec", ["dd", "qd"])
+def test_set_launch_every_choice(prec):
+    """Every launch a caller can fix with polyeval_set_launch (chunks 1..8,
+    both shapes) gives the same outputs up to the summation order of the
+    chunks, within the tolerance of the exact oracle at sampled points."""
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+    from _util import QD_TOL, pe_precision
+
+    s, pts = synth.config(2, n_points=100)
+    if prec == "qd":
+        rng = np.random.Generator(np.random.PCG64(116))
+        s, pts = s.to_qd(117), synth.widen_qd(rng, pts)
+    ev = pkg.PolyEval(s, pe_precision(prec), max_points=100)
+    x = to_device(pts)
+    for chunks in (1, 3, 8):
+        for shape in (1, 2):
+            pkg.polyeval_set_launch(ev.handle, 100, chunks, shape)
+            f, J = ev.eval(x)
+            torch.cuda.synchronize()
+            assert ev.status() == pkg.PE_OK
+            check_exact_oracle(s, pts, f.cpu().numpy(), J.cpu().numpy(), QD_TOL if prec == "qd" else DD_TOL,
+                               points_idx=[0, 99], polys=[5])
+    pkg.polyeval_set_launch(ev.handle, 100, 0, 0)  # back to the built-in choice
+    with pytest.raises(pkg.PolyEvalError):
+        pkg.polyeval_set_launch(ev.handle, 100, 9, 1)
