@@ -363,6 +363,44 @@ def track_leg(pkg, torch):
     return out
 
 
+# The experiment shapes of the paper's Tables 1 and 2 (Section 4): n = 32,
+# k = 9 with powers at most 2, and k = 16 with powers at most 10, each with 22,
+# 32 and 48 monomials per polynomial; the paper times 100,000 evaluations.
+PAPER_SHAPES = [(9, 2, 22), (9, 2, 32), (9, 2, 48), (16, 10, 22), (16, 10, 32), (16, 10, 48)]
+PAPER_EVALS = 100_000
+
+
+def paper_tables(pkg, torch):
+    """Time PAPER_EVALS evaluations (one batch) of a synthetic system of each
+    shape in double-double (FP64 pipe and integer pipes) and in double."""
+    rows = []
+    for i, (k, d, m) in enumerate(PAPER_SHAPES):
+        s = synth.regular_system(synth.SEED_BASE + 800 + i, 32, m, k, d)
+        pts = synth.points(synth.SEED_BASE + 900 + i, 32, PAPER_EVALS)
+        row = {"k": k, "max_power": d, "monomials": 32 * m}
+        for name, code in (("dd", pkg.PE_DD), ("ddint", pkg.PE_DD_INT), ("f64", pkg.PE_F64)):
+            sk = s.as_fp64() if code == pkg.PE_F64 else s
+            x = torch.from_numpy(np.ascontiguousarray(pts[..., [0, 2]]) if code == pkg.PE_F64 else pts).cuda()
+            ev = pkg.PolyEval(sk, code, max_points=PAPER_EVALS)
+            f, J = ev.eval(x)  # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record()
+            for _ in range(reps):
+                ev.eval(x, f, J)
+            e1.record()
+            torch.cuda.synchronize()
+            assert ev.status() == pkg.PE_OK
+            ms = e0.elapsed_time(e1) / reps
+            row[name] = {"ms": ms, "us_per_eval": 1e3 * ms / PAPER_EVALS, "evals_per_s": PAPER_EVALS / (ms * 1e-3)}
+            ev.close()
+            del x, f, J
+        rows.append(row)
+    return {"evaluations": PAPER_EVALS, "n": 32, "shapes": rows,
+            "data": "synthetic systems of the shapes of Tables 1-2, unit-circle points, one batch"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -378,6 +416,8 @@ def main():
     ap.add_argument("--graph", action="store_true",
                     help="replay the evaluation from a captured CUDA graph in the timed steps")
     ap.add_argument("--no-tracker", action="store_true", help="skip the path-tracking leg")
+    ap.add_argument("--paper-tables", action="store_true",
+                    help="time the experiment shapes of the paper's Tables 1-2 and print their JSON object")
     ap.add_argument("--only-tracker", action="store_true",
                     help="run only the path-tracking leg and print its JSON object (for profiling the tracker)")
     ap.add_argument("--config", type=int, default=CONFIG_INDEX, choices=[2, 3, 4, 5],
@@ -402,6 +442,13 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    if args.paper_tables:
+        out = paper_tables(pkg, torch)
+        if rank == 0:
+            print(json.dumps({"paper_tables": out}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.only_tracker:
         out = track_leg(pkg, torch)
         if rank == 0:
