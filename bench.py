@@ -650,7 +650,8 @@ def main():
                                      "complex double-double in/out, products in 128-bit integer block floating point"),
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "cuda_graph": bool(args.graph),
-                       "autotuned_launch": {k: {"chunks": v[0], "shape": "one wave" if v[1] == 1 else "persistent"}
+                       "autotuned_launch": {k: {"chunks": v[0], "shape": "one wave" if v[1] == 1 else "persistent",
+                                                "monomial_groups_per_warp": v[2]}
                                             for k, v in tuned.items()},
                        "launch": f"{kernels // max(args.steps, 1)} kernels per step (power table, monomial "
                                  "kernel, combine of monomial chunks when the call has few items)"},

@@ -202,27 +202,32 @@ PE_API int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out
 /*
  * Choose the launch of polyeval_eval for P points by timing the candidates on
  * the caller's data: the number of chunks the monomials of each polynomial
- * are split into (1, 2, 4, 8, as the handle's scratch allows) and the launch
+ * are split into (1, 2, 4, 8, as the handle's scratch allows), the launch
  * shape (1: one single-warp block per work item, all resident at once; 2: a
- * persistent grid taking items from the work counter).  Runs each candidate
- * four times on `stream` (one warm-up, three timed with CUDA events),
- * synchronises, keeps the fastest in the handle for later calls with the same
- * P, and returns it in *chunks and *shape (either may be NULL).  The outputs
- * hold a valid evaluation on return.  Not for use during stream capture.
- * Errors: those of polyeval_eval.
+ * persistent grid taking items from the work counter) and, for PE_DD and
+ * PE_F64 calls with fewer than 64 points, the threads per monomial: groups
+ * G = 1, 2, 4, 8, 16 of a warp work on G monomials at once, each group of
+ * 32 / G lanes on 16 / G points.  Runs each candidate four times on `stream`
+ * (one warm-up, three timed with CUDA events), synchronises, keeps the
+ * fastest in the handle for later calls with the same P, and returns it in
+ * *chunks, *shape and *groups (any may be NULL).  The outputs hold a valid
+ * evaluation on return.  Not for use during stream capture.  Errors: those of
+ * polyeval_eval.
  */
 PE_API int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream,
-                             int *chunks, int *shape);
+                             int *chunks, int *shape, int *groups);
 
 /*
  * Set the launch polyeval_eval uses for calls with exactly P points (what
  * polyeval_autotune would store): chunks 1..8 monomial chunks per polynomial
- * (capped by the handle's scratch at run time) and shape 1 (one single-warp
- * block per work item) or 2 (persistent grid).  0 for either leaves that
- * choice to the built-in heuristic; chunks = shape = 0 removes the entry.
+ * (capped by the handle's scratch at run time), shape 1 (one single-warp
+ * block per work item) or 2 (persistent grid), and groups 1, 2, 4, 8 or 16
+ * monomial groups per warp (PE_DD and PE_F64; ignored by the integer-pipe
+ * precisions).  0 for any leaves that choice to the built-in heuristic (for
+ * groups: the largest G with G P <= 16); all 0 removes the entry.
  * Single-system handles.  Errors: PE_EINVAL.
  */
-PE_API int polyeval_set_launch(polyeval_t *h, int64_t P, int chunks, int shape);
+PE_API int polyeval_set_launch(polyeval_t *h, int64_t P, int chunks, int shape, int groups);
 
 /*
  * One Newton step x <- x + dx, J(x) dx = -f(x), at P points of a square

@@ -114,9 +114,9 @@ def load_library(path: Optional[str] = None):
         "polyeval_fp64_peak": ([P, D, D], ctypes.c_int),
         "polyeval_eval_noalloc": ([ctypes.POINTER(pe_system), I32, I32, P, I64, P, P, P], ctypes.c_int),
         "polyeval_newton": ([P, P, I64, P, P, P, P], ctypes.c_int),
-        "polyeval_autotune": ([P, P, I64, P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
-                              ctypes.c_int),
-        "polyeval_set_launch": ([P, I64, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "polyeval_autotune": ([P, P, I64, P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "polyeval_set_launch": ([P, I64, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "polyeval_track_defaults": ([ctypes.c_int, ctypes.POINTER(pe_track_params)], ctypes.c_int),
         "polyeval_bezout": ([P, D, ctypes.POINTER(I32)], ctypes.c_int),
         "polyeval_start_points": ([P, I64, I64, P, P], ctypes.c_int),
@@ -230,16 +230,16 @@ def polyeval_eval(h: int, points, P: int, out_f, out_J, stream=None) -> None:
 
 def polyeval_autotune(h: int, points, P: int, out_f, out_J, stream=None):
     """Time the launch candidates for P points and keep the fastest in the
-    handle; returns (chunks, shape)."""
-    c, m = ctypes.c_int(), ctypes.c_int()
+    handle; returns (chunks, shape, groups)."""
+    c, m, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(load_library().polyeval_autotune(h, _addr(points), int(P), _addr(out_f), _addr(out_J), _stream(stream),
-                                            ctypes.byref(c), ctypes.byref(m)), "polyeval_autotune")
-    return c.value, m.value
+                                            ctypes.byref(c), ctypes.byref(m), ctypes.byref(g)), "polyeval_autotune")
+    return c.value, m.value, g.value
 
 
-def polyeval_set_launch(h: int, P: int, chunks: int = 0, shape: int = 0) -> None:
+def polyeval_set_launch(h: int, P: int, chunks: int = 0, shape: int = 0, groups: int = 0) -> None:
     """Fix the launch for calls with P points (0 = built-in choice)."""
-    _check(load_library().polyeval_set_launch(h, int(P), int(chunks), int(shape)), "polyeval_set_launch")
+    _check(load_library().polyeval_set_launch(h, int(P), int(chunks), int(shape), int(groups)), "polyeval_set_launch")
 
 
 def polyeval_newton(h: int, points, P: int, out_f, out_J, norms=None, stream=None) -> None:
@@ -383,7 +383,7 @@ class PolyEval:
         return out_f, out_J
 
     def autotune(self, points, out_f=None, out_J=None, stream=None):
-        """Tune the launch for this point count; returns (chunks, shape)."""
+        """Tune the launch for this point count; returns (chunks, shape, groups)."""
         import torch
 
         c = _elem(self.precision)

@@ -59,7 +59,11 @@ struct ArithDD {
   __device__ static V im_signed(const Full &x, unsigned long long m) { return negate_if(x.im, m); }
   __device__ static V neg_if(V x, unsigned long long m) { return negate_if(x, m); }
   __device__ static V sel(bool t, V a, V b) { return select(t, a, b); }
-  __device__ static V partner(V x) { return shfl_xor(x, 1); }
+  __device__ static V partner(V x, unsigned pm) {
+    return dd{__shfl_xor_sync(pm, x.h, 1), __shfl_xor_sync(pm, x.l, 1)};
+  }
+  __device__ static F f_merge(F a, F b) { return pe::add(a, b); }
+  __device__ static F f_xor(F a, int d) { return shfl_xor(a, d); }
   __device__ static V dot(V a1, V b1, V a2, V b2) { return dot2(a1, b1, a2, b2); }
   __device__ static V dotn(V a1, V b1, V a2, V b2) { return dot2n(a1, b1, a2, b2); }
   __device__ static V add(V a, V b) { return pe::add(a, b); }
@@ -103,7 +107,13 @@ struct ArithF64 {
   __device__ static V im_signed(const Full &x, unsigned long long m) { return negate_if(x.im, m); }
   __device__ static V neg_if(V x, unsigned long long m) { return negate_if(x, m); }
   __device__ static V sel(bool t, V a, V b) { return select(t, a, b); }
-  __device__ static V partner(V x) { return shfl_xor(x, 1); }
+  __device__ static V partner(V x, unsigned pm) { return __shfl_xor_sync(pm, x, 1); }
+  __device__ static F f_merge(F a, F b) {  // (s1 + e1) + (s2 + e2) with the rounding error of s1 + s2 kept
+    double s, e;
+    two_sum(a.h, b.h, s, e);
+    return dd{s, __dadd_rn(__dadd_rn(a.l, b.l), e)};
+  }
+  __device__ static F f_xor(F a, int d) { return shfl_xor(a, d); }
   __device__ static V dot(V a1, V b1, V a2, V b2) { return __fma_rn(a1, b1, __dmul_rn(a2, b2)); }
   __device__ static V dotn(V a1, V b1, V a2, V b2) { return dot(a1, b1, a2, b2); }
   __device__ static V add(V a, V b) { return __dadd_rn(a, b); }
@@ -129,18 +139,22 @@ struct ArithF64 {
 //   re: X.re y.re - X.im y.im     im: X.re y.im + X.im y.re
 // i.e. X.re * y_own + (sign * X.im) * y_partner with sign -1 on real lanes.
 // Norm: renormalise the result (for a product that feeds another product).
+// pm: the mask of the lane pair (the whole warp when every lane works on the
+// same monomial; the pair's two lanes when groups of the warp may diverge).
 template <class A, bool Norm>
-__device__ __forceinline__ typename A::V mul_x(typename A::V y, const typename A::Full &X, unsigned long long sgn) {
-  const typename A::V yp = A::partner(y);
+__device__ __forceinline__ typename A::V mul_x(typename A::V y, const typename A::Full &X, unsigned long long sgn,
+                                               unsigned pm) {
+  const typename A::V yp = A::partner(y, pm);
   return Norm ? A::dotn(X.re, y, A::im_signed(X, sgn), yp) : A::dot(X.re, y, A::im_signed(X, sgn), yp);
 }
 
 // P * Q with both factors split across the lane pair:
 //   re lane: P.re Q.re - P.im Q.im      im lane: P.im Q.re + P.re Q.im
 template <class A, bool Norm = false>
-__device__ __forceinline__ typename A::V mul_split(typename A::V P, typename A::V Q, int c, unsigned long long sgn) {
-  const typename A::V Pp = A::partner(P);
-  const typename A::V Qp = A::partner(Q);
+__device__ __forceinline__ typename A::V mul_split(typename A::V P, typename A::V Q, int c, unsigned long long sgn,
+                                                   unsigned pm) {
+  const typename A::V Pp = A::partner(P, pm);
+  const typename A::V Qp = A::partner(Q, pm);
   const bool re = (c == 0);
   return Norm ? A::dotn(P, A::sel(re, Q, Qp), A::neg_if(Pp, sgn), A::sel(re, Qp, Q))
               : A::dot(P, A::sel(re, Q, Qp), A::neg_if(Pp, sgn), A::sel(re, Qp, Q));
@@ -148,8 +162,8 @@ __device__ __forceinline__ typename A::V mul_split(typename A::V P, typename A::
 
 // 1 / z for z split over the lane pair: conj(z) / |z|^2.
 template <class A>
-__device__ __forceinline__ typename A::V recip_split(typename A::V z, int c) {
-  const typename A::V zp = A::partner(z);
+__device__ __forceinline__ typename A::V recip_split(typename A::V z, int c, unsigned pm) {
+  const typename A::V zp = A::partner(z, pm);
   const typename A::V n2 = A::dotn(z, z, zp, zp);  // |z|^2, the same on both lanes
   return A::mul_real(A::neg_if(z, c ? kSign : 0ULL), A::recip_real(n2));
 }

@@ -96,7 +96,8 @@ struct polyeval {
   struct Tuned {
     int64_t P;
     int chunks;
-    int mode;  // 1: one single-warp block per item, 2: persistent grid
+    int mode;    // 1: one single-warp block per item, 2: persistent grid
+    int groups;  // monomial groups per warp (0: built-in choice)
   };
   std::vector<Tuned> tuned;  // launch choices found by polyeval_autotune, per point count
   // timing of the main kernel
@@ -313,7 +314,9 @@ int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, b
 
 int finish_handle(polyeval *h, Compiled &c) {
   h->kmax = c.kmax;
-  h->kslots = std::max(c.kmax - 1, 1);
+  // forward products k - 1 per monomial; the grouped kernel also parks the k
+  // derivative terms in the slots
+  h->kslots = block_format(h) ? std::max(c.kmax - 1, 1) : std::max(c.kmax, 1);
   if ((h->wide && h->kslots > kWideSlotsFull) || (h->qd && h->kslots > kQdSlotsFull)) {
     // keep every second forward product (the others are recomputed in the
     // backward pass) so that enough warps fit in shared memory
@@ -463,6 +466,8 @@ pe::MainParams main_params(const polyeval *h) {
   p.items = static_cast<const int2 *>(h->items.p);
   p.table = static_cast<const double *>(h->table.p);
   p.kslots = h->kslots;
+  p.tile_points = pe::kPointsPerWarp;
+  p.groups = 1;
   p.slot_stride = h->slot_stride;
   p.n_polys_total = h->n_polys_total;
   p.counter = static_cast<unsigned *>(h->counter.p);
@@ -714,8 +719,16 @@ namespace {
 // One single-system evaluation.  chunks > 0 and mode > 0 force the monomial
 // chunk count and the launch shape (used by the autotuner); 0 picks them from
 // the tuned table or the heuristic.
+// Monomial groups per warp for P points: enough that the lane pairs of a warp
+// are busy when P < 16 (the largest power of two G with G P <= 16).
+int default_groups(int64_t P) {
+  int G = 1;
+  while (G < 16 && 2 * G * P <= pe::kPointsPerWarp) G *= 2;
+  return G;
+}
+
 int eval_single(polyeval *h, const void *points, int64_t P, void *out_f, void *out_J, cudaStream_t s, int chunks,
-                int mode) {
+                int mode, int groups = 0) {
   if (!h || h->batch || P < 0) return PE_EINVAL;
   if (P == 0) return PE_OK;
   if (P > h->max_points) return PE_ERANGE;
@@ -767,20 +780,26 @@ int eval_single(polyeval *h, const void *points, int64_t P, void *out_f, void *o
   mp.out_f = static_cast<double *>(out_f);
   mp.out_J = static_cast<double *>(out_J);
   mp.single_P = static_cast<int32_t>(P);
-  mp.single_T = static_cast<int32_t>((P + pe::kPointsPerWarp - 1) / pe::kPointsPerWarp);
+  if (chunks <= 0 || mode <= 0 || groups <= 0) {
+    for (const auto &t : h->tuned)
+      if (t.P == P) {
+        if (chunks <= 0) chunks = t.chunks;
+        if (mode <= 0) mode = t.mode;
+        if (groups <= 0) groups = t.groups;
+      }
+  }
+  // monomial groups per warp (double-double and double kernels only)
+  int G = block_format(h) ? 1 : (groups > 0 ? groups : default_groups(P));
+  if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16) G = 1;
+  mp.groups = G;
+  mp.tile_points = pe::kPointsPerWarp / G;
+  mp.single_T = static_cast<int32_t>((P + mp.tile_points - 1) / mp.tile_points);
   const int64_t base = static_cast<int64_t>(d.N) * mp.single_T;
   // Few (polynomial, tile) items: split each polynomial's monomials into
   // chunks so that about one wave of resident warps has work.
   int C = 1;
   const int64_t capacity = static_cast<int64_t>(h->sms) * h->blocks_per_sm_1;
   const size_t per_chunk = outputs_bytes(h, P);
-  if (chunks <= 0 || mode <= 0) {
-    for (const auto &t : h->tuned)
-      if (t.P == P) {
-        if (chunks <= 0) chunks = t.chunks;
-        if (mode <= 0) mode = t.mode;
-      }
-  }
   if (base > 0 && per_chunk > 0) {
     // about one wave of items; the quad-double kernel, whose long carry
     // chains leave it latency bound, gains from about two (measured: 4
@@ -798,6 +817,7 @@ int eval_single(polyeval *h, const void *points, int64_t P, void *out_f, void *o
   mp.scratch_f = static_cast<double *>(h->scratch.p);
   mp.scratch_J = C > 1 ? mp.scratch_f + static_cast<size_t>(C - 1) * f_doubles : nullptr;
   mp.n_items = base * C;
+  if (mp.n_items > INT32_MAX) return PE_ERANGE;  // the work counter is 32-bit
   int rc = run_main(h, mp, s, mode);
   if (rc != PE_OK) return rc;
   if (h->qd) {  // add the chunks' accumulators, round to quad-double
@@ -828,18 +848,19 @@ int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, voi
 }
 
 int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream,
-                      int *chunks, int *shape) {
+                      int *chunks, int *shape, int *groups) {
   if (!h || h->batch || P < 1) return PE_EINVAL;
   if (P > h->max_points) return PE_ERANGE;
-  if (!points || !out_f || !out_J) return PE_EINVAL;
+  if (!points || !out_f || !out_J || !arrays_aligned(points, out_f, out_J)) return PE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const SysDesc &d = h->sys[0];
-  const int64_t base = static_cast<int64_t>(d.N) * ((P + pe::kPointsPerWarp - 1) / pe::kPointsPerWarp);
   const int64_t capacity = static_cast<int64_t>(h->sms) * h->blocks_per_sm_1;
   const size_t per_chunk = outputs_bytes(h, P);
   const int max_c = per_chunk ? static_cast<int>(std::min<int64_t>(
                                     kMaxChunks, 1 + static_cast<int64_t>(h->scratch.bytes / per_chunk)))
                               : 1;
+  // monomial groups: tried when the call has fewer points than 4 tiles
+  const int max_g = block_format(h) || P >= 4 * pe::kPointsPerWarp ? 1 : 16;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -848,23 +869,29 @@ int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void *out_f,
   const bool timing = h->timing;
   h->timing = false;
   float best = 0.0f;
-  int best_c = 1, best_m = 2;
+  int best_c = 1, best_m = 2, best_g = 1;
   int rc = PE_OK;
-  for (int C = 1; C <= max_c && rc == PE_OK; C *= 2) {
-    for (int m = 1; m <= 2 && rc == PE_OK; m++) {
-      if (m == 1 && base * C > capacity) continue;  // one wave only when every item is resident
-      rc = eval_single(h, points, P, out_f, out_J, s, C, m);  // warm-up
-      if (rc != PE_OK) break;
-      if (cudaEventRecord(e0, s) != cudaSuccess) rc = PE_ECUDA;
-      for (int r = 0; r < 3 && rc == PE_OK; r++) rc = eval_single(h, points, P, out_f, out_J, s, C, m);
-      if (rc == PE_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
-        rc = PE_ECUDA;
-      float ms = 0.0f;
-      if (rc == PE_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = PE_ECUDA;
-      if (rc == PE_OK && (best == 0.0f || ms < best)) {
-        best = ms;
-        best_c = C;
-        best_m = m;
+  for (int G = 1; G <= max_g && rc == PE_OK; G *= 2) {
+    const int64_t tp = pe::kPointsPerWarp / G;
+    const int64_t base = static_cast<int64_t>(d.N) * ((P + tp - 1) / tp);
+    for (int C = 1; C <= max_c && rc == PE_OK; C *= 2) {
+      if (base * C > INT32_MAX) continue;
+      for (int m = 1; m <= 2 && rc == PE_OK; m++) {
+        if (m == 1 && base * C > capacity) continue;  // one wave only when every item is resident
+        rc = eval_single(h, points, P, out_f, out_J, s, C, m, G);  // warm-up
+        if (rc != PE_OK) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) rc = PE_ECUDA;
+        for (int r = 0; r < 3 && rc == PE_OK; r++) rc = eval_single(h, points, P, out_f, out_J, s, C, m, G);
+        if (rc == PE_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+          rc = PE_ECUDA;
+        float ms = 0.0f;
+        if (rc == PE_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = PE_ECUDA;
+        if (rc == PE_OK && (best == 0.0f || ms < best)) {
+          best = ms;
+          best_c = C;
+          best_m = m;
+          best_g = G;
+        }
       }
     }
   }
@@ -877,23 +904,26 @@ int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void *out_f,
     if (t.P == P) {
       t.chunks = best_c;
       t.mode = best_m;
+      t.groups = best_g;
       found = true;
     }
-  if (!found) h->tuned.push_back(polyeval::Tuned{P, best_c, best_m});
+  if (!found) h->tuned.push_back(polyeval::Tuned{P, best_c, best_m, best_g});
   if (chunks) *chunks = best_c;
   if (shape) *shape = best_m;
+  if (groups) *groups = best_g;
   return PE_OK;
 }
 
 
-int polyeval_set_launch(polyeval_t *h, int64_t P, int chunks, int shape) {
+int polyeval_set_launch(polyeval_t *h, int64_t P, int chunks, int shape, int groups) {
   if (!h || h->batch || P < 1 || chunks < 0 || chunks > kMaxChunks || shape < 0 || shape > 2) return PE_EINVAL;
+  if (groups != 0 && groups != 1 && groups != 2 && groups != 4 && groups != 8 && groups != 16) return PE_EINVAL;
   for (auto it = h->tuned.begin(); it != h->tuned.end(); ++it)
     if (it->P == P) {
       h->tuned.erase(it);
       break;
     }
-  if (chunks > 0 || shape > 0) h->tuned.push_back(polyeval::Tuned{P, chunks, shape});
+  if (chunks > 0 || shape > 0 || groups > 0) h->tuned.push_back(polyeval::Tuned{P, chunks, shape, groups});
   return PE_OK;
 }
 

@@ -43,6 +43,8 @@ struct MainParams {
   int64_t n_items;
   int32_t single_P;         // >= 0: single-system handle evaluated at single_P points
   int32_t single_T;         // tiles of a single-system call
+  int32_t tile_points;      // points per tile: kPointsPerWarp / groups
+  int32_t groups;           // monomial groups per warp (1, 2, 4, 8, 16; double-double and double only)
   int32_t kslots;           // prefix-product slots per lane (max k - 1, at least 1)
   int32_t slot_stride;      // integer path: every slot_stride-th forward product is kept
   int32_t n_polys_total;

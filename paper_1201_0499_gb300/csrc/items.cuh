@@ -40,7 +40,7 @@ __device__ __forceinline__ bool decode_item(const MainParams &kp, unsigned item,
     it.s = (x.x >= 0 && x.x < kp.n_polys_total) ? kp.poly_sys[x.x] : 0;
     it.P = kp.sys[it.s].P;
   }
-  if (it.gp < 0 || it.gp >= kp.n_polys_total || it.tile * kPointsPerWarp >= it.P) {
+  if (it.gp < 0 || it.gp >= kp.n_polys_total || it.tile * kp.tile_points >= it.P) {
     if (lane == 0) atomicOr(kp.status, 1);
     return false;
   }

@@ -91,7 +91,7 @@ __device__ void process_item(const MainParams &kp, const Item &it, typename A::V
     // product absorbs at O(u^2) cost; two in a row would let it grow.
     bool renorm = false;
     auto chain = [&](V y, const Full &X) {
-      const V r = renorm ? mul_x<A, true>(y, X, sgn) : mul_x<A, false>(y, X, sgn);
+      const V r = renorm ? mul_x<A, true>(y, X, sgn, kFull) : mul_x<A, false>(y, X, sgn, kFull);
       renorm = !renorm;
       return r;
     };
@@ -112,7 +112,7 @@ __device__ void process_item(const MainParams &kp, const Item &it, typename A::V
     const uint32_t wl = __ldg(vw + k - 1);
     const int vl = static_cast<int>(wl & 0xffffu), al = static_cast<int>(wl >> 16);
     const Full xl = A::load_full(xel(vl));
-    f = A::f_add(f, mul_x<A, false>(Pc, xl, sgn));
+    f = A::f_add(f, mul_x<A, false>(Pc, xl, sgn, kFull));
     accumulate<A>(jel(vl), c, valid, al == 1 ? Pc : A::mul_int(Pc, static_cast<double>(al)));
     // Stage 2, backward: Q = x_{i_{j+2}} ... x_{i_k}; derivative by x_{i_{j+1}} = a_{j+1} slot_j Q
     V Q = A::comp(xl, c);
@@ -120,7 +120,7 @@ __device__ void process_item(const MainParams &kp, const Item &it, typename A::V
     for (int j = k - 2; j >= 0; j--) {
       const uint32_t w = __ldg(vw + j);
       const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
-      const V D = mul_split<A>(smem[j * 32 + lane], Q, c, sgn);
+      const V D = mul_split<A>(smem[j * 32 + lane], Q, c, sgn, kFull);
       accumulate<A>(jel(v), c, valid, a == 1 ? D : A::mul_int(D, static_cast<double>(a)));
       if (j > 0) Q = chain(Q, A::load_full(xel(v)));
     }
@@ -135,8 +135,115 @@ __device__ void process_item(const MainParams &kp, const Item &it, typename A::V
   }
 }
 
-template <class A>
-__global__ void __launch_bounds__(kWarpsPerBlockMax * 32) main_kernel(const MainParams kp) {
+// The same with G monomial groups per warp (G = 2, 4, 8, 16): each group of
+// 32 / G lanes holds the 16 / G points of the tile (lanes 2q, 2q+1 of the
+// group: point q) and the G groups take monomials t0 + g, t0 + g + G, ... of
+// the polynomial, so that a
+// call with few points keeps every lane busy (the "threads per monomial"
+// choice: 32 / G lanes per monomial).  Groups of one round may have monomials
+// of different k and diverge, so the partner shuffles use the pair's mask.
+// Each group keeps its derivative terms in its slots and the groups add them
+// into the row J[p, :] one after another (two monomials of a round may share
+// a variable); f is summed per group and across the groups at the end.
+template <class A, int G>
+__device__ void process_item_groups(const MainParams &kp, const Item &it, typename A::V *smem, int lane) {
+  constexpr int GL = 32 / G;                     // lanes per group
+  constexpr int QP = kPointsPerWarp / G;         // points per tile
+  const int gp = it.gp, tile = it.tile, s = it.s, P = it.P;
+  using V = typename A::V;
+  using Full = typename A::Full;
+  constexpr int KD = A::kDoubles;
+  const SysDesc sd = kp.sys[s];
+  const int n = sd.n;
+  const int g = lane / GL;
+  const int q = tile * QP + ((lane % GL) >> 1);
+  const bool valid = q < P;
+  const int qc = valid ? q : P - 1;
+  const int c = lane & 1;
+  const unsigned long long sgn = c ? 0ULL : kSign;
+  const unsigned pm = 3u << (lane & 30);
+  const size_t Pz = static_cast<size_t>(P);
+  const int pl = gp - sd.poly0;
+  const double *X = kp.points + static_cast<size_t>(sd.pt_off) * KD;
+  const double *Tb = kp.table + static_cast<size_t>(sd.tab_off) * KD;
+  double *Jrow = it.J_base + (static_cast<size_t>(sd.J_off) + static_cast<size_t>(pl) * n * Pz) * KD;
+
+  auto xel = [&](int v) { return X + (static_cast<size_t>(v) * Pz + qc) * KD; };
+  auto tel = [&](int e, int v) { return Tb + ((static_cast<size_t>(e - 2) * n + v) * Pz + qc) * KD; };
+  auto jel = [&](int v) { return Jrow + (static_cast<size_t>(v) * Pz + qc) * KD; };
+
+  if (valid && g == 0)
+    for (int v = 0; v < n; v++) A::store_comp(jel(v), c, A::zero());
+  __syncwarp();
+
+  typename A::F f = A::f_zero();
+  const int t0 = it.t0, t1 = it.t1;
+  for (int base = t0; base < t1; base += G) {
+    const int t = base + g;
+    const bool has = t < t1;  // uniform over the group
+    int k = 0;
+    const uint32_t *vw = nullptr;
+    if (has) {
+      const int vb = kp.mono_ptr[t];
+      k = kp.mono_ptr[t + 1] - vb;
+      vw = kp.var + vb;
+      V Gv = A::load_comp_ro(kp.coef + static_cast<size_t>(t) * KD, c);
+      if (k == 0) {
+        f = A::f_add(f, Gv);
+      } else {
+        bool renorm = false;
+        auto chain = [&](V y, const Full &Xf) {
+          const V r = renorm ? mul_x<A, true>(y, Xf, sgn, pm) : mul_x<A, false>(y, Xf, sgn, pm);
+          renorm = !renorm;
+          return r;
+        };
+        for (int j = 0; j < k; j++) {
+          const uint32_t w = __ldg(vw + j);
+          const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
+          if (a >= 2) Gv = chain(Gv, A::load_full(a == 2 ? xel(v) : tel(a - 1, v)));
+        }
+        V Pc = Gv;
+        for (int j = 0; j < k - 1; j++) {
+          smem[j * 32 + lane] = Pc;
+          const int v = static_cast<int>(__ldg(vw + j) & 0xffffu);
+          Pc = chain(Pc, A::load_full(xel(v)));
+        }
+        const uint32_t wl = __ldg(vw + k - 1);
+        const int vl = static_cast<int>(wl & 0xffffu), al = static_cast<int>(wl >> 16);
+        const Full xl = A::load_full(xel(vl));
+        f = A::f_add(f, mul_x<A, false>(Pc, xl, sgn, pm));
+        // derivative terms into the slots: slot j <- term of x_{i_{j+1}}
+        V Q = A::comp(xl, c);
+        renorm = false;
+        for (int j = k - 2; j >= 0; j--) {
+          const int a = static_cast<int>(__ldg(vw + j) >> 16);
+          const V D = mul_split<A>(smem[j * 32 + lane], Q, c, sgn, pm);
+          smem[j * 32 + lane] = a == 1 ? D : A::mul_int(D, static_cast<double>(a));
+          if (j > 0) Q = chain(Q, A::load_full(xel(static_cast<int>(__ldg(vw + j) & 0xffffu))));
+        }
+        smem[(k - 1) * 32 + lane] = al == 1 ? Pc : A::mul_int(Pc, static_cast<double>(al));
+      }
+    }
+    __syncwarp();
+    for (int r = 0; r < G; r++) {  // the groups' terms into J, one group at a time
+      if (g == r && k > 0)
+        for (int j = 0; j < k; j++) accumulate<A>(jel(static_cast<int>(__ldg(vw + j) & 0xffffu)), c, valid, smem[j * 32 + lane]);
+      __syncwarp();
+    }
+  }
+  for (int d = GL; d < 32; d <<= 1) f = A::f_merge(f, A::f_xor(f, d));
+  if (valid && g == 0) {
+    A::store_comp(it.f_base + (static_cast<size_t>(sd.f_off) + static_cast<size_t>(pl) * Pz + q) * KD, c,
+                  A::f_finish(f));
+    for (int v = 0; v < n; v++) {
+      double *p = jel(v);
+      A::store_comp(p, c, A::finish(A::load_comp(p, c)));
+    }
+  }
+}
+
+template <class A, int G>
+__global__ void main_kernel(const MainParams kp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   typename A::V *smem = reinterpret_cast<typename A::V *>(smem_raw) + static_cast<size_t>(warp) * kp.kslots * 32;
@@ -147,7 +254,10 @@ __global__ void __launch_bounds__(kWarpsPerBlockMax * 32) main_kernel(const Main
     if (static_cast<int64_t>(item) >= kp.n_items) break;
     Item it;
     if (!decode_item(kp, item, lane, it)) continue;
-    process_item<A>(kp, it, smem, lane);
+    if constexpr (G == 1)
+      process_item<A>(kp, it, smem, lane);
+    else
+      process_item_groups<A, G>(kp, it, smem, lane);
   }
 }
 
@@ -240,29 +350,51 @@ cudaError_t launch_powers(bool dd, const PowerParams &p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <class A>
+cudaError_t prepare_main_t(int v) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(main_kernel<A, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) ||
+      (e = cudaFuncSetAttribute(main_kernel<A, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) ||
+      (e = cudaFuncSetAttribute(main_kernel<A, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) ||
+      (e = cudaFuncSetAttribute(main_kernel<A, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) ||
+      (e = cudaFuncSetAttribute(main_kernel<A, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)))
+    return e;
+  return cudaSuccess;
+}
+
 cudaError_t prepare_main(bool dd, size_t smem_bytes) {
   // Every handle launches with at most the device's opt-in limit; setting the
   // attribute to that limit once keeps it valid for all handles.
   const int v = static_cast<int>(smem_bytes);
-  return dd ? cudaFuncSetAttribute(main_kernel<ArithDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)
-            : cudaFuncSetAttribute(main_kernel<ArithF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+  return dd ? prepare_main_t<ArithDD>(v) : prepare_main_t<ArithF64>(v);
 }
 
 cudaError_t main_occupancy(bool dd, int warps_per_block, size_t smem_bytes, int *blocks_per_sm) {
-  return dd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<ArithDD>, warps_per_block * 32,
-                                                            smem_bytes)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<ArithF64>, warps_per_block * 32,
-                                                            smem_bytes);
+  return dd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<ArithDD, 1>,
+                                                            warps_per_block * 32, smem_bytes)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<ArithF64, 1>,
+                                                            warps_per_block * 32, smem_bytes);
+}
+
+template <class A>
+cudaError_t launch_main_t(const MainParams &p, int warps_per_block, size_t smem_bytes, int grid, cudaStream_t s) {
+  const dim3 b(warps_per_block * 32);
+  switch (p.groups) {
+    case 1: main_kernel<A, 1><<<grid, b, smem_bytes, s>>>(p); break;
+    case 2: main_kernel<A, 2><<<grid, b, smem_bytes, s>>>(p); break;
+    case 4: main_kernel<A, 4><<<grid, b, smem_bytes, s>>>(p); break;
+    case 8: main_kernel<A, 8><<<grid, b, smem_bytes, s>>>(p); break;
+    case 16: main_kernel<A, 16><<<grid, b, smem_bytes, s>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_main(bool dd, const MainParams &p, int warps_per_block, size_t smem_bytes, int grid,
                         cudaStream_t s) {
   if (p.n_items <= 0) return cudaSuccess;
-  if (dd)
-    main_kernel<ArithDD><<<grid, warps_per_block * 32, smem_bytes, s>>>(p);
-  else
-    main_kernel<ArithF64><<<grid, warps_per_block * 32, smem_bytes, s>>>(p);
-  return cudaGetLastError();
+  return dd ? launch_main_t<ArithDD>(p, warps_per_block, smem_bytes, grid, s)
+            : launch_main_t<ArithF64>(p, warps_per_block, smem_bytes, grid, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -465,8 +465,8 @@ def test_autotune_then_eval(prec):
     s, pts = synth.config(2, n_points=300)
     ev = pkg.PolyEval(s, pe_precision(prec), max_points=300)
     x = to_device(pts)
-    chunks, shape = ev.autotune(x)
-    assert chunks in (1, 2, 4, 8) and shape in (1, 2)
+    chunks, shape, groups = ev.autotune(x)
+    assert chunks in (1, 2, 4, 8) and shape in (1, 2) and groups == 1  # 300 points: no groups tried
     f, J = ev.eval(x)
     torch.cuda.synchronize()
     assert ev.status() == pkg.PE_OK
@@ -500,3 +500,37 @@ def test_set_launch_every_choice(prec):
     pkg.polyeval_set_launch(ev.handle, 100, 0, 0)  # back to the built-in choice
     with pytest.raises(pkg.PolyEvalError):
         pkg.polyeval_set_launch(ev.handle, 100, 9, 1)
+
+
+@pytest.mark.parametrize("prec", ["dd", "f64"])
+@pytest.mark.parametrize("P", [1, 3, 5, 15])
+def test_monomial_groups_few_points(prec, P):
+    """Few points: G monomial groups per warp (32 / G lanes per monomial).
+    Monomials of different k in one polynomial make the groups of a round
+    diverge; two monomials of a round may share variables.  Every G against
+    the exact oracle, every output."""
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+    from _util import pe_precision
+
+    s = random_system(118, n=10, N=5, m=23, kmin=0, kmax=6, emax=4)
+    pts = synth.points(119, 10, P)
+    if prec == "f64":
+        s64, p64 = fp64_inputs(s, pts)
+    ev = pkg.PolyEval(s if prec == "dd" else s.as_fp64(), pe_precision(prec), max_points=P)
+    x = to_device(pts, prec == "dd")
+    for G in (1, 2, 4, 8, 16):
+        for chunks in (1, 3):
+            pkg.polyeval_set_launch(ev.handle, P, chunks, 0, G)
+            f, J = ev.eval(x)
+            torch.cuda.synchronize()
+            assert ev.status() == pkg.PE_OK
+            f, J = f.cpu().numpy(), J.cpu().numpy()
+            if prec == "f64":
+                from _util import widen
+
+                f, J = widen(f), widen(J)
+            check_exact_oracle(s, pts, f, J, tol(prec), dd=prec == "dd")
+    g = ev.autotune(x)[2]
+    assert g in (1, 2, 4, 8, 16)
