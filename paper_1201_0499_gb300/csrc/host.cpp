@@ -91,7 +91,10 @@ struct polyeval {
   // path tracking (single square systems): degrees of the polynomials and
   // the tracker's scratch, allocated on first use
   std::vector<int32_t> degrees;
-  DeviceBuf deg_dev, tr_f, tr_J, tr_xs, tr_state, tr_active, tr_x64, tr_status, tr_xc, tr_statc, tr_idx, tr_JL, tr_bL;
+  DeviceBuf deg_dev, tr_f, tr_J, tr_active, tr_x64, tr_status, tr_xc, tr_statc, tr_idx, tr_JL, tr_bL;
+  // working copies of the paths (two, for compaction), their original
+  // indices, the states of paths already written home, the running list
+  DeviceBuf tr_xw[2], tr_xsw[2], tr_stw[2], tr_perm[2], tr_home, tr_list;
   cudaStream_t tr_stream = nullptr;  // the tracker's own stream (graph capture needs one)
   struct Tuned {
     int64_t P;
@@ -1098,11 +1101,16 @@ int track_scratch(polyeval *h, int64_t P) {
   const SysDesc &d = h->sys[0];
   const size_t eb = static_cast<size_t>(elem_doubles(h)) * sizeof(double);
   const size_t np = static_cast<size_t>(d.n) * static_cast<size_t>(P);
+  const size_t Pz = static_cast<size_t>(P);
   int rc;
   if ((rc = upload_degrees(h)) || (rc = ensure(h->tr_f, eb * np)) || (rc = ensure(h->tr_J, eb * np * d.n)) ||
-      (rc = ensure(h->tr_xs, eb * np)) || (rc = ensure(h->tr_state, sizeof(pe::TrackState) * static_cast<size_t>(P))) ||
-      (rc = ensure(h->tr_active, sizeof(unsigned))))
+      (rc = ensure(h->tr_active, sizeof(unsigned))) || (rc = ensure(h->tr_home, sizeof(pe::TrackState) * Pz)) ||
+      (rc = ensure(h->tr_list, sizeof(int64_t) * Pz)))
     return rc;
+  for (int b = 0; b < 2; b++)
+    if ((rc = ensure(h->tr_xw[b], eb * np)) || (rc = ensure(h->tr_xsw[b], eb * np)) ||
+        (rc = ensure(h->tr_stw[b], sizeof(pe::TrackState) * Pz)) || (rc = ensure(h->tr_perm[b], sizeof(int64_t) * Pz)))
+      return rc;
   return PE_OK;
 }
 
@@ -1115,21 +1123,26 @@ bool params_ok(const pe_track_params *p) {
 
 constexpr int kGraphIters = 8;  // tracker iterations per captured graph
 
-int track(polyeval *h, const pe_track_params *prm, double *x, int64_t P, double *t_out, int32_t *status,
+// Compaction: once at most half of the working batch still runs (and the
+// batch has at least kCompactMin paths), every path is written home to the
+// caller's array (by its original index) and the running ones are packed into
+// a batch of their own, so that the long tail of slow paths no longer pays
+// for evaluating the finished ones.
+constexpr int64_t kCompactMin = 128;
+
+int track(polyeval *h, const pe_track_params *prm, double *x_home, int64_t P0, double *t_out, int32_t *status,
           int64_t *iterations, cudaStream_t s) {
   if (iterations) *iterations = 0;
-  if (P == 0) return PE_OK;
-  int rc = track_scratch(h, P);
+  if (P0 == 0) return PE_OK;
+  int rc = track_scratch(h, P0);
   if (rc != PE_OK) return rc;
   const SysDesc &d = h->sys[0];
+  const int words = elem_doubles(h);
+  const int state_words = static_cast<int>(sizeof(pe::TrackState) / sizeof(double));
   pe::TrackParams tp{};
   tp.n = d.n;
-  tp.P = P;
   tp.J = static_cast<double *>(h->tr_J.p);
   tp.f = static_cast<double *>(h->tr_f.p);
-  tp.x = x;
-  tp.xs = static_cast<double *>(h->tr_xs.p);
-  tp.st = static_cast<pe::TrackState *>(h->tr_state.p);
   tp.deg = static_cast<const int32_t *>(h->deg_dev.p);
   tp.gre = prm->gamma_re;
   tp.gim = prm->gamma_im;
@@ -1143,28 +1156,49 @@ int track(polyeval *h, const pe_track_params *prm, double *x, int64_t P, double 
   tp.succ_grow = prm->succ_grow;
   tp.mixed = prm->mixed != 0 && h->dd;
   if (tp.mixed) {  // double copies of the systems, for warp solves outside shared memory
-    const size_t np = static_cast<size_t>(d.n) * static_cast<size_t>(P);
+    const size_t np = static_cast<size_t>(d.n) * static_cast<size_t>(P0);
     if ((rc = ensure(h->tr_JL, 16 * np * d.n)) || (rc = ensure(h->tr_bL, 16 * np))) return rc;
     tp.JL = static_cast<double *>(h->tr_JL.p);
     tp.bL = static_cast<double *>(h->tr_bL.p);
   }
   tp.active = static_cast<unsigned *>(h->tr_active.p);
   // The iterations run on the handle's own stream: the batch of kGraphIters
-  // iterations (counter reset, evaluation, step) is captured once into a CUDA
-  // graph and replayed, which removes the host overhead of its dozens of
-  // short launches; the running-path count is read after each replay.
+  // iterations (counter reset, evaluation, step) is captured into a CUDA graph
+  // and replayed, which removes the host overhead of its dozens of short
+  // launches; the running-path count is read after each replay.
   if (!h->tr_stream && cudaStreamCreateWithFlags(&h->tr_stream, cudaStreamNonBlocking) != cudaSuccess) {
     h->tr_stream = nullptr;
     return PE_ECUDA;
   }
   cudaStream_t ts = h->tr_stream;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PE_ECUDA;  // start points queued by the caller
+  auto xw = [&](int b) { return static_cast<double *>(h->tr_xw[b].p); };
+  auto xsw = [&](int b) { return static_cast<double *>(h->tr_xsw[b].p); };
+  auto stw = [&](int b) { return static_cast<double *>(h->tr_stw[b].p); };
+  auto perm = [&](int b) { return static_cast<double *>(h->tr_perm[b].p); };  // int64 bits, moved as words
+  int cur = 0;
+  int64_t Pc = P0;
+  {  // working batch 0: the start points, paths in order
+    std::vector<int64_t> iota(static_cast<size_t>(P0));
+    std::iota(iota.begin(), iota.end(), int64_t{0});
+    if (cudaMemcpy(perm(0), iota.data(), sizeof(int64_t) * iota.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpyAsync(xw(0), x_home, static_cast<size_t>(words) * sizeof(double) * d.n * P0,
+                        cudaMemcpyDeviceToDevice, ts) != cudaSuccess)
+      return PE_ECUDA;
+  }
+  auto bind = [&]() {
+    tp.P = Pc;
+    tp.x = xw(cur);
+    tp.xs = xsw(cur);
+    tp.st = reinterpret_cast<pe::TrackState *>(stw(cur));
+  };
+  bind();
   if (pe::launch_track_init(h->dd, tp, prm->h_init, ts) != cudaSuccess) return PE_ECUDA;
   const bool timing = h->timing;
   h->timing = false;  // no event pairs inside the graph
   auto iteration = [&](cudaStream_t st) -> int {
     if (cudaMemsetAsync(tp.active, 0, sizeof(unsigned), st) != cudaSuccess) return PE_ECUDA;
-    int r = polyeval_eval(h, x, P, tp.f, tp.J, st);
+    int r = polyeval_eval(h, tp.x, tp.P, tp.f, tp.J, st);
     if (r != PE_OK) return r;
     if (pe::launch_track_step(h->dd, tp, st) != cudaSuccess) return PE_ECUDA;
     h->kernels_launched++;
@@ -1173,29 +1207,69 @@ int track(polyeval *h, const pe_track_params *prm, double *x, int64_t P, double 
   struct Graph {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t e = nullptr;
-    ~Graph() {
+    void reset() {
       if (e) cudaGraphExecDestroy(e);
       if (g) cudaGraphDestroy(g);
+      e = nullptr;
+      g = nullptr;
     }
+    ~Graph() { reset(); }
   } graph;
   int64_t per_replay = 0;
-  if (prm->max_iters >= kGraphIters) {
+  auto capture = [&]() -> int {  // a graph of kGraphIters iterations on the current batch
+    graph.reset();
+    if (prm->max_iters < kGraphIters) return PE_OK;
     const int64_t k0 = h->kernels_launched;
-    if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = PE_ECUDA;
-    for (int i = 0; i < kGraphIters && rc == PE_OK; i++) rc = iteration(ts);
+    int r = cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) == cudaSuccess ? PE_OK : PE_ECUDA;
+    for (int i = 0; i < kGraphIters && r == PE_OK; i++) r = iteration(ts);
     const cudaError_t ce = cudaStreamEndCapture(ts, &graph.g);  // always leave capture mode
-    if (rc == PE_OK && (ce != cudaSuccess || cudaGraphInstantiate(&graph.e, graph.g, 0) != cudaSuccess)) rc = PE_ECUDA;
+    if (r == PE_OK && (ce != cudaSuccess || cudaGraphInstantiate(&graph.e, graph.g, 0) != cudaSuccess)) r = PE_ECUDA;
     per_replay = h->kernels_launched - k0;
     h->kernels_launched = k0;
-    if (rc != PE_OK) {
-      cudaGetLastError();
-      h->timing = timing;
-      return rc;
-    }
-  }
+    if (r != PE_OK) cudaGetLastError();
+    return r;
+  };
+  // every working path (and its state) home, by original index
+  auto write_home = [&]() -> int {
+    const int64_t *pm = static_cast<const int64_t *>(h->tr_perm[cur].p);
+    if (pe::launch_move_paths(xw(cur), Pc, x_home, P0, pm, Pc, d.n, words, true, ts) != cudaSuccess ||
+        pe::launch_move_paths(stw(cur), Pc, static_cast<double *>(h->tr_home.p), P0, pm, Pc, 1, state_words, true,
+                              ts) != cudaSuccess)
+      return PE_ECUDA;
+    return PE_OK;
+  };
+  // the running paths into the other working batch
+  auto compact = [&]() -> int {
+    std::vector<pe::TrackState> st(static_cast<size_t>(Pc));
+    if (cudaMemcpyAsync(st.data(), stw(cur), sizeof(pe::TrackState) * st.size(), cudaMemcpyDeviceToHost, ts) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ts) != cudaSuccess)
+      return PE_ECUDA;
+    std::vector<int64_t> keep;
+    for (int64_t q = 0; q < Pc; q++)
+      if (st[static_cast<size_t>(q)].status == pe::kPathRunning) keep.push_back(q);
+    const int64_t m = static_cast<int64_t>(keep.size());
+    int r = write_home();
+    if (r != PE_OK || m == 0) return r;
+    const int64_t *list = static_cast<const int64_t *>(h->tr_list.p);
+    const int nx = 1 - cur;
+    if (cudaMemcpyAsync(h->tr_list.p, keep.data(), sizeof(int64_t) * keep.size(), cudaMemcpyHostToDevice, ts) !=
+            cudaSuccess ||
+        pe::launch_move_paths(xw(cur), Pc, xw(nx), m, list, m, d.n, words, false, ts) != cudaSuccess ||
+        pe::launch_move_paths(xsw(cur), Pc, xsw(nx), m, list, m, d.n, words, false, ts) != cudaSuccess ||
+        pe::launch_move_paths(stw(cur), Pc, stw(nx), m, list, m, 1, state_words, false, ts) != cudaSuccess ||
+        pe::launch_move_paths(perm(cur), Pc, perm(nx), m, list, m, 1, 1, false, ts) != cudaSuccess ||
+        cudaStreamSynchronize(ts) != cudaSuccess)  // `keep` is read by the copy
+      return PE_ECUDA;
+    cur = nx;
+    Pc = m;
+    bind();
+    return capture();
+  };
+  rc = capture();
   int64_t it = 0;
   unsigned running = 1;
-  while (it < prm->max_iters && running && rc == PE_OK) {
+  while (rc == PE_OK && it < prm->max_iters && running) {
     if (graph.e && it + kGraphIters <= prm->max_iters) {
       if (cudaGraphLaunch(graph.e, ts) != cudaSuccess) rc = PE_ECUDA;
       h->kernels_launched += per_replay;
@@ -1208,10 +1282,14 @@ int track(polyeval *h, const pe_track_params *prm, double *x, int64_t P, double 
                             cudaSuccess ||
                         cudaStreamSynchronize(ts) != cudaSuccess))
       rc = PE_ECUDA;
+    if (rc == PE_OK && running && Pc >= kCompactMin && 2 * static_cast<int64_t>(running) <= Pc) rc = compact();
   }
   h->timing = timing;
+  if (rc == PE_OK) rc = write_home();
   if (rc != PE_OK) return rc;
-  if (pe::launch_track_finish(tp.st, P, t_out, status, ts) != cudaSuccess) return PE_ECUDA;
+  if (pe::launch_track_finish(static_cast<const pe::TrackState *>(h->tr_home.p), P0, t_out, status, ts) !=
+      cudaSuccess)
+    return PE_ECUDA;
   if (iterations) *iterations = it;
   return cudaStreamSynchronize(ts) == cudaSuccess ? PE_OK : PE_ECUDA;
 }

@@ -257,6 +257,31 @@ def test_track_large_batch(prec):
     assert exact_residual(system_for(s, prec), np.ascontiguousarray(sample)) <= tol
 
 
+@pytest.mark.parametrize("prec", ["f64", "dd"])
+def test_track_half_the_paths_diverge(prec):
+    """256 paths, 128 finite solutions: six decoupled quadrics with known
+    roots and x6^2 = 1, x6 x7 = 2 (two finite solutions, the other two paths of
+    that block go to infinity).  Half the paths end early, so the batch is
+    compacted while the rest run; the successes must be exactly the 128
+    solutions and the others must not succeed."""
+    rng = np.random.Generator(np.random.PCG64(622))
+    roots = [(complex(*rng.standard_normal(2)), complex(*rng.standard_normal(2))) for _ in range(6)]
+    polys, coef = [], []
+    for v, (r1, r2) in enumerate(roots):
+        c = np.convolve([1.0, -r1], [1.0, -r2])
+        polys.append([([v], [2]), ([v], [1]), ([], [])])
+        coef += [[c[0].real, 0, c[0].imag, 0], [c[1].real, 0, c[1].imag, 0], [c[2].real, 0, c[2].imag, 0]]
+    polys.append([([6], [2]), ([], [])])
+    coef += [[1, 0, 0, 0], [-1, 0, 0, 0]]
+    polys.append([([6, 7], [1, 1]), ([], [])])
+    coef += [[1, 0, 0, 0], [-2, 0, 0, 0]]
+    s = synth.from_monomials(8, polys, coef)
+    z, raw, st, _, _ = run_track(s, prec)
+    assert len(st) == 256 and int(np.sum(st == 1)) == 128 and np.all(st != 0)
+    want = [list(r) + [x6, 2 / x6] for r in itertools.product(*roots) for x6 in (1.0, -1.0)]
+    assert match([z[i] for i in np.flatnonzero(st == 1)], want, 1e-9)
+
+
 def test_track_no_finite_solutions():
     s = synth.from_monomials(2, [[([0, 1], [1, 1]), ([], [])], [([0, 1], [1, 1]), ([], [])]],
                              [[1, 0, 0, 0], [-1, 0, 0, 0], [1, 0, 0, 0], [-2, 0, 0, 0]])
