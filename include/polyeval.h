@@ -401,7 +401,11 @@ typedef struct {
 #define PE_PATH_DIVERGED 3      /* max|x| exceeded x_big                           */
 #define PE_PATH_END_NOT_CONVERGED 4 /* at t = 1 Newton did not reach end_tol (singular or ill-conditioned end point) */
 
-/* Default tracking parameters for a precision (PE_DD, PE_DD_INT or PE_F64). */
+/* Default tracking parameters for a precision (PE_DD, PE_DD_INT or PE_F64):
+ * gamma = exp(i), h_init 0.02, h_min 1e-14 (double-double) or 1e-10, h_max 0.1,
+ * corr_tol 1e-6, end_tol 1e-26 (double-double) or 1e-13, x_big 1e8,
+ * max_corr 3, max_end 8, succ_grow 3, mixed 1 for double-double,
+ * max_iters 100000. */
 PE_API int polyeval_track_defaults(int precision, pe_track_params *prm);
 
 /* The Bezout number prod d_i (the number of paths) as a double, and the
