@@ -24,7 +24,7 @@ tolerance and is computed in float64.
 from __future__ import annotations
 
 import math
-from typing import List, Sequence, Tuple
+from typing import Sequence, Tuple
 
 # ----------------------------------------------------------------------------
 # exact complex dyadic numbers: (A, B, E) means (A + iB) * 2**E

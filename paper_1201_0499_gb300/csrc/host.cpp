@@ -291,8 +291,8 @@ int append_system(Compiled &c, const pe_system *s, int32_t sys_index, bool dd, b
       if (dd || wide) {
         // renormalised (FastTwoSum after ordering), so the first product of a
         // chain starts from |lo| <= ulp(hi)/2 whatever the caller passed
-        auto renorm = [](double a, double b, double &hi, double &lo) {
-          const double big = std::fabs(a) >= std::fabs(b) ? a : b, small = std::fabs(a) >= std::fabs(b) ? b : a;
+        auto renorm = [](double u, double w, double &hi, double &lo) {
+          const double big = std::fabs(u) >= std::fabs(w) ? u : w, small = std::fabs(u) >= std::fabs(w) ? w : u;
           hi = big + small;
           lo = small - (hi - big);
         };

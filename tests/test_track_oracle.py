@@ -10,7 +10,6 @@ solutions (the Bezout number).
 import itertools
 
 import numpy as np
-import pytest
 
 import synth
 from oracle import exact as E
