@@ -282,6 +282,20 @@ def test_track_half_the_paths_diverge(prec):
     assert match([z[i] for i in np.flatnonzero(st == 1)], want, 1e-9)
 
 
+@pytest.mark.parametrize("prec", ["f64", "dd"])
+def test_track_double_root_is_not_reported_as_converged(prec):
+    """(x - 1)^2 = 0, y^2 = 2: every path ends at a double root in x, where
+    Newton's method converges only linearly, so no path may report success;
+    the paths end either with a failed step size or with a non-converged end
+    point, and then near x = 1 with y^2 = 2."""
+    s = synth.from_monomials(2, [[([0], [2]), ([0], [1]), ([], [])], [([1], [2]), ([], [])]],
+                             [[1, 0, 0, 0], [-2, 0, 0, 0], [1, 0, 0, 0], [1, 0, 0, 0], [-2, 0, 0, 0]])
+    z, raw, st, _, _ = run_track(s, prec)
+    assert len(st) == 4 and np.all((st == 2) | (st == 4)), st
+    for q in np.flatnonzero(st == 4):
+        assert abs(z[q, 0] - 1) < 1e-3 and abs(z[q, 1] ** 2 - 2) < 1e-6
+
+
 def test_track_no_finite_solutions():
     s = synth.from_monomials(2, [[([0, 1], [1, 1]), ([], [])], [([0, 1], [1, 1]), ([], [])]],
                              [[1, 0, 0, 0], [-1, 0, 0, 0], [1, 0, 0, 0], [-2, 0, 0, 0]])
