@@ -150,14 +150,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside), "window": window}
 
 
-def cpu_oracle_rate(system, pts, seconds: float = 10.0, max_points=None):
-    """The C double-double oracle on the host cores: evaluations per second,
-    repeating the batch (or its first max_points points) for ~`seconds`."""
+def cpu_oracle_rate(system, pts, seconds: float = 10.0, max_points=None, threads=None):
+    """The C double-double oracle on the host cores (all of them, or
+    `threads`): evaluations per second, repeating the batch (or its first
+    max_points points) for ~`seconds`."""
     import oracle
 
     P = pts.shape[1] if max_points is None else min(max_points, pts.shape[1])
     sub = np.ascontiguousarray(pts[:, :P])
-    threads = oracle.max_threads()
+    threads = oracle.max_threads() if threads is None else threads
     out = (np.zeros((system.n_polys, P, 4)), np.zeros((system.n_polys, system.n_vars, P, 4)))
     reps, t0 = 0, time.perf_counter()
     while True:
@@ -629,7 +630,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == CONFIG_INDEX:
         rate, cores, sample = cpu_oracle_rate(wl.system, wl.pts, seconds=10.0)
-        cpu = {"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample}
+        rate1, _c1, sample1 = cpu_oracle_rate(wl.system, wl.pts, seconds=5.0, max_points=64, threads=1)
+        cpu = {"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "single_core": {"value": rate1, "sample": sample1}}
 
     if rank == 0:
         line = {
