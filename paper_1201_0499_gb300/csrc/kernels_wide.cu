@@ -131,11 +131,18 @@ __device__ void process_item_wide(const MainParams &kp, const Item &it, uint32_t
       continue;
     }
     const uint32_t *vw = kp.var + vb;
+    // chain products: every second one normalised (see wide::mul_x)
+    bool norm = false;
+    auto chain = [&](const WV &y, const WF &X) {
+      const WV r = norm ? wide::mul_x<true>(y, X, c) : wide::mul_x<false>(y, X, c);
+      norm = !norm;
+      return r;
+    };
     // Stage 1: G = c * prod_{a_j >= 2} x_{i_j}^(a_j - 1)
     for (int j = 0; j < k; j++) {
       const uint32_t w = __ldg(vw + j);
       const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
-      if (a >= 2) G = wide::mul_x(G, wide::load_wf(tel(a - 1, v)), c);
+      if (a >= 2) G = chain(G, wide::load_wf(tel(a - 1, v)));
     }
     // Stage 2, forward: P_j = G x_{i_1} ... x_{i_j}; every kp.slot_stride-th
     // one is kept (slot j / stride), the others are recomputed below
@@ -144,15 +151,16 @@ __device__ void process_item_wide(const MainParams &kp, const Item &it, uint32_t
     for (int j = 0; j < k - 1; j++) {
       if (j % stride == 0) store_slot(slots, j / stride, lane, Pc);
       const int v = static_cast<int>(__ldg(vw + j) & 0xffffu);
-      Pc = wide::mul_x(Pc, wide::load_wf(tel(1, v)), c);
+      Pc = chain(Pc, wide::load_wf(tel(1, v)));
     }
     const uint32_t wl = __ldg(vw + k - 1);
     const int vl = static_cast<int>(wl & 0xffffu), al = static_cast<int>(wl >> 16);
     const WF xl = wide::load_wf(tel(1, vl));
-    f = add(f, wide::to_dd(wide::mul_x(Pc, xl, c)));
+    f = add(f, wide::to_dd(wide::mul_x<false>(Pc, xl, c)));  // to_dd takes any leading bit
     accumulate_dd(jel(vl), c, valid, wide::to_dd(al == 1 ? Pc : wide::mul_small(Pc, static_cast<uint32_t>(al))));
     // Stage 2, backward
     WV Q = wide::component(xl, c);
+    norm = false;
     for (int j = k - 2; j >= 0; j--) {
       const uint32_t w = __ldg(vw + j);
       const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
@@ -161,7 +169,7 @@ __device__ void process_item_wide(const MainParams &kp, const Item &it, uint32_t
         Pj = wide::mul_x(Pj, wide::load_wf(tel(1, static_cast<int>(__ldg(vw + r) & 0xffffu))), c);
       const WV D = wide::mul_pair(Pj, Q, c);
       accumulate_dd(jel(v), c, valid, wide::to_dd(a == 1 ? D : wide::mul_small(D, static_cast<uint32_t>(a))));
-      if (j > 0) Q = wide::mul_x(Q, wide::load_wf(tel(1, v)), c);
+      if (j > 0) Q = chain(Q, wide::load_wf(tel(1, v)));
     }
   }
   if (valid) {

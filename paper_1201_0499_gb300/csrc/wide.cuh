@@ -229,8 +229,14 @@ __device__ __forceinline__ WV normalize_pair(const WV &v) {
   return WV{shr(v.m, -sh), v.s, v.e - sh};
 }
 
-// y (split over the pair) times X (full value on both lanes), normalised:
+// y (split over the pair) times X (full value on both lanes), normalised
+// when Norm:
 //   re: X.re y.re - X.im y.im      im: X.re y.im + X.im y.re
+// Unnormalised, the pair's larger magnitude lies in [2^121, 2^125) (the
+// product of normalised operands, top half, plus one sum); a product of such
+// an operand keeps 2 fewer significant bits, still about 2^-118, so chains
+// normalise only every second product.
+template <bool Norm = true>
 __device__ __forceinline__ WV mul_x(const WV &y, const WF &X, int c) {
   const Mag yp = shfl_xor_mag(y.m, 1);
   const uint32_t sp = __shfl_xor_sync(0xffffffffu, y.s, 1);
@@ -240,6 +246,7 @@ __device__ __forceinline__ WV mul_x(const WV &y, const WF &X, int c) {
   const uint32_t s2 = ((X.signs << 1) & kSignBit) ^ sp ^ (c == 0 ? kSignBit : 0u);
   uint32_t s;
   const Mag r = signed_add(p1, s1, p2, s2, s);
+  if (!Norm) return WV{r, s, X.e + y.e + 128};
   return normalize_pair(WV{r, s, X.e + y.e + 128});
 }
 
