@@ -348,9 +348,9 @@ int finish_handle(polyeval *h, Compiled &c) {
     if (pe::main_wide_occupancy(1, per_warp, &h->blocks_per_sm_1) != cudaSuccess) return PE_ECUDA;
   } else {
     if (pe::prepare_main(h->dd, static_cast<size_t>(optin)) != cudaSuccess) return PE_ECUDA;
-    if (pe::main_occupancy(h->dd, h->warps_per_block, h->smem_bytes, &h->blocks_per_sm) != cudaSuccess)
+    if (pe::main_occupancy(h->dd, h->batch, h->warps_per_block, h->smem_bytes, &h->blocks_per_sm) != cudaSuccess)
       return PE_ECUDA;
-    if (pe::main_occupancy(h->dd, 1, per_warp, &h->blocks_per_sm_1) != cudaSuccess) return PE_ECUDA;
+    if (pe::main_occupancy(h->dd, h->batch, 1, per_warp, &h->blocks_per_sm_1) != cudaSuccess) return PE_ECUDA;
   }
   if (h->blocks_per_sm < 1 || h->blocks_per_sm_1 < 1) return PE_ERANGE;
   int rc;
@@ -661,7 +661,11 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
         flops += c.poly_flops[gp] * P;
         for (int32_t tl = 0; tl < d.tiles; tl++) {
           const int32_t in_tile = static_cast<int32_t>(std::min<int64_t>(pe::kPointsPerWarp, P - tl * pe::kPointsPerWarp));
-          items.push_back(Item{gp, tl, c.poly_ops[gp] * in_tile});
+          // a partial last tile spreads its points over monomial groups
+          int lg = 0;
+          if (!block_format(h))
+            while ((2 << lg) * in_tile <= pe::kPointsPerWarp && lg < 4) lg++;
+          items.push_back(Item{gp, tl | (lg << pe::kTileBits), c.poly_ops[gp] * in_tile});
         }
       }
     }

@@ -11,6 +11,10 @@ namespace pe {
 // part and lane 2q+1 the imaginary part of every value of point q.
 constexpr int kPointsPerWarp = 16;
 constexpr int kWarpsPerBlockMax = 4;
+// A batch item's tile word: the 16-point tile index in bits 0..26 and log2 of
+// its monomial groups per warp in bits 27..29 (groups > 1 for the last,
+// partial tile of a system with double-double or double arithmetic).
+constexpr int kTileBits = 27;
 
 // One compiled system inside a handle.  Offsets are in complex elements of
 // the handle's precision.
@@ -74,7 +78,7 @@ struct PowerParams {
 cudaError_t launch_powers(bool dd, const PowerParams &p, cudaStream_t s);
 cudaError_t launch_main(bool dd, const MainParams &p, int warps_per_block, size_t smem_bytes, int grid,
                         cudaStream_t s);
-cudaError_t main_occupancy(bool dd, int warps_per_block, size_t smem_bytes, int *blocks_per_sm);
+cudaError_t main_occupancy(bool dd, bool batch, int warps_per_block, size_t smem_bytes, int *blocks_per_sm);
 cudaError_t prepare_main(bool dd, size_t smem_bytes);
 cudaError_t fp64_peak_probe(cudaStream_t s, double *fma_per_s, double *sm_clock_mhz);
 

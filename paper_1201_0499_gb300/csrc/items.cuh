@@ -15,7 +15,8 @@
 namespace pe {
 
 struct Item {
-  int gp, tile, s, P;  // global polynomial, tile, system, points of the system
+  int gp, tile, s, P;  // global polynomial, tile (of 16 / groups points), system, points of the system
+  int groups;          // monomial groups per warp
   int t0, t1;          // monomial range
   double *f_base;      // output (or scratch) base for f
   double *J_base;      // output (or scratch) base for J
@@ -33,14 +34,17 @@ __device__ __forceinline__ bool decode_item(const MainParams &kp, unsigned item,
     it.gp = kp.perm[r];
     it.s = 0;
     it.P = kp.single_P;
+    it.groups = kp.groups;
   } else {
     const int2 x = kp.items[item];
     it.gp = x.x;
-    it.tile = x.y;
+    it.groups = 1 << ((x.y >> kTileBits) & 7);
+    it.tile = (x.y & ((1 << kTileBits) - 1)) * it.groups;  // in tiles of 16 / groups points
     it.s = (x.x >= 0 && x.x < kp.n_polys_total) ? kp.poly_sys[x.x] : 0;
     it.P = kp.sys[it.s].P;
   }
-  if (it.gp < 0 || it.gp >= kp.n_polys_total || it.tile * kp.tile_points >= it.P) {
+  if (it.gp < 0 || it.gp >= kp.n_polys_total || it.groups > kPointsPerWarp ||
+      it.tile * (kPointsPerWarp / it.groups) >= it.P) {
     if (lane == 0) atomicOr(kp.status, 1);
     return false;
   }

@@ -350,6 +350,30 @@ cudaError_t launch_powers(bool dd, const PowerParams &p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Batch handles: each item carries its own number of monomial groups (the
+// last, partial tile of a system spreads its few points over the warp).
+template <class A>
+__global__ void main_kernel_batch(const MainParams kp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  typename A::V *smem = reinterpret_cast<typename A::V *>(smem_raw) + static_cast<size_t>(warp) * kp.kslots * 32;
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(kp.counter, 1u);
+    item = __shfl_sync(kFull, item, 0);
+    if (static_cast<int64_t>(item) >= kp.n_items) break;
+    Item it;
+    if (!decode_item(kp, item, lane, it)) continue;
+    switch (it.groups) {
+      case 2: process_item_groups<A, 2>(kp, it, smem, lane); break;
+      case 4: process_item_groups<A, 4>(kp, it, smem, lane); break;
+      case 8: process_item_groups<A, 8>(kp, it, smem, lane); break;
+      case 16: process_item_groups<A, 16>(kp, it, smem, lane); break;
+      default: process_item<A>(kp, it, smem, lane); break;
+    }
+  }
+}
+
 template <class A>
 cudaError_t prepare_main_t(int v) {
   cudaError_t e;
@@ -357,7 +381,8 @@ cudaError_t prepare_main_t(int v) {
       (e = cudaFuncSetAttribute(main_kernel<A, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) ||
       (e = cudaFuncSetAttribute(main_kernel<A, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) ||
       (e = cudaFuncSetAttribute(main_kernel<A, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) ||
-      (e = cudaFuncSetAttribute(main_kernel<A, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)))
+      (e = cudaFuncSetAttribute(main_kernel<A, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) ||
+      (e = cudaFuncSetAttribute(main_kernel_batch<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)))
     return e;
   return cudaSuccess;
 }
@@ -369,16 +394,22 @@ cudaError_t prepare_main(bool dd, size_t smem_bytes) {
   return dd ? prepare_main_t<ArithDD>(v) : prepare_main_t<ArithF64>(v);
 }
 
-cudaError_t main_occupancy(bool dd, int warps_per_block, size_t smem_bytes, int *blocks_per_sm) {
-  return dd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<ArithDD, 1>,
-                                                            warps_per_block * 32, smem_bytes)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<ArithF64, 1>,
-                                                            warps_per_block * 32, smem_bytes);
+cudaError_t main_occupancy(bool dd, bool batch, int warps_per_block, size_t smem_bytes, int *blocks_per_sm) {
+  const int t = warps_per_block * 32;
+  if (batch)
+    return dd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel_batch<ArithDD>, t, smem_bytes)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel_batch<ArithF64>, t, smem_bytes);
+  return dd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<ArithDD, 1>, t, smem_bytes)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<ArithF64, 1>, t, smem_bytes);
 }
 
 template <class A>
 cudaError_t launch_main_t(const MainParams &p, int warps_per_block, size_t smem_bytes, int grid, cudaStream_t s) {
   const dim3 b(warps_per_block * 32);
+  if (p.single_P < 0) {
+    main_kernel_batch<A><<<grid, b, smem_bytes, s>>>(p);
+    return cudaGetLastError();
+  }
   switch (p.groups) {
     case 1: main_kernel<A, 1><<<grid, b, smem_bytes, s>>>(p); break;
     case 2: main_kernel<A, 2><<<grid, b, smem_bytes, s>>>(p); break;
