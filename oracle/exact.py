@@ -136,6 +136,26 @@ def cx_to_dd(x) -> Tuple[float, float, float, float]:
     return tuple(out)
 
 
+def real_to_parts(m: int, e: int, parts: int):
+    """m * 2**e as `parts` doubles: each the nearest double to what the parts
+    before it leave (a normalised multi-double)."""
+    out = []
+    for _ in range(parts):
+        d = _int_to_float_scaled(m, e)
+        out.append(d)
+        md, ed = dyadic(d)
+        emin = min(ed, e)
+        m = (m << (e - emin)) - (md << (ed - emin))
+        e = emin
+    return out
+
+
+def cx_to_qd(x) -> Tuple[float, ...]:
+    """Round an exact value to a complex quad-double (re0..re3, im0..im3),
+    each component a normalised sum of four doubles."""
+    return tuple(real_to_parts(x[0], x[2], 4) + real_to_parts(x[1], x[2], 4))
+
+
 # ----------------------------------------------------------------------------
 # evaluation by definition (Section 2, Eq. 1)
 # ----------------------------------------------------------------------------

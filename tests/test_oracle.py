@@ -395,6 +395,26 @@ def test_planted_mistake_is_caught(name, monkeypatch):
 # exact helpers
 # ----------------------------------------------------------------------------
 
+def test_qd_rounding_round_trip_and_bound():
+    """A normalised quad-double is its own rounding; rounding an exact value
+    to quad-double errs by at most 2^-211 of it (four parts of 53 bits, each
+    rounded to nearest); the parts are normalised."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    vals = synth.widen_qd(rng, synth.random_cdd(rng, 50))
+    for v in vals:
+        assert E.cx_to_qd(E.cx_from_dd(v)) == tuple(float(x) for x in v)
+    for i in range(50):
+        # an exact product of three quad-doubles needs about 640 bits
+        z = E.cx_mul(E.cx_mul(E.cx_from_dd(vals[i]), E.cx_from_dd(vals[(i + 1) % 50])), E.cx_from_dd(vals[(i + 2) % 50]))
+        r = E.cx_to_qd(z)
+        err = E.cx_abs(E.cx_sub(E.cx_from_dd(r), z))
+        assert err <= 2.0 ** -211 * E.cx_abs(z)
+        for c in (0, 4):
+            for k in range(3):
+                hi, lo = r[c + k], r[c + k + 1]
+                assert abs(lo) <= math.ulp(hi) / 2 or hi == 0.0
+
+
 def test_dd_round_trip_and_rounding():
     rng = np.random.Generator(np.random.PCG64(9))
     v = synth.random_cdd(rng, 200)
