@@ -245,9 +245,17 @@ PE_API int polyeval_set_launch(polyeval_t *h, int64_t P, int chunks, int shape, 
  *   stream  as polyeval_eval
  * The solve is LU with partial pivoting per point (pivot of largest modulus)
  * in the handle's precision (double-double for PE_DD and PE_DD_INT, double
- * for PE_F64), one warp per point.  Allocates nothing.  Errors: those of
- * polyeval_eval; PE_EINVAL for a batch handle, a non-square system or a
- * PE_QD_INT handle.
+ * for PE_F64), 4 to 32 lanes of a warp per point.  PE_QD_INT handles
+ * evaluate f and J in quad-double and solve for dx in double-double from
+ * the leading two parts of each component (mixed precision, as iterative
+ * refinement: each step gains about 104 bits less log2 cond(J) until x
+ * reaches quad-double accuracy); x + dx is summed exactly and rounded to
+ * quad-double.  There out_f holds dx with parts 2, 3 zero and out_J the
+ * double-double factors in parts 0, 1 (parts 2, 3 zero).  Allocates nothing,
+ * except on a PE_QD_INT handle with n > 22, whose first call allocates
+ * 32 n (n + 1) max_points bytes of double-double scratch for the handle.
+ * Errors: those of polyeval_eval; PE_EINVAL for a batch handle or a
+ * non-square system; PE_ENOMEM when that scratch cannot be allocated.
  */
 PE_API int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, void *out_J, double *norms,
                            void *stream);

@@ -95,6 +95,7 @@ struct polyeval {
   // working copies of the paths (two, for compaction), their original
   // indices, the states of paths already written home, the running list
   DeviceBuf tr_xw[2], tr_xsw[2], tr_stw[2], tr_perm[2], tr_home, tr_list;
+  DeviceBuf nt_Jdd, nt_fdd;  // quad-double Newton: double-double systems too large for shared memory
   cudaStream_t tr_stream = nullptr;  // the tracker's own stream (graph capture needs one)
   struct Tuned {
     int64_t P;
@@ -118,6 +119,8 @@ struct polyeval {
 namespace {
 
 int elem_doubles(const polyeval *h) { return h->qd ? 8 : h->dd ? 4 : 2; }
+
+int ensure(DeviceBuf &b, size_t bytes) { return b.bytes >= bytes ? PE_OK : b.alloc(bytes); }
 
 // Device arrays are read and written with 16-byte vector accesses.
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -935,9 +938,14 @@ int polyeval_set_launch(polyeval_t *h, int64_t P, int chunks, int shape, int gro
 }
 
 int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, void *out_J, double *norms, void *stream) {
-  if (!h || h->batch || h->qd) return PE_EINVAL;
+  if (!h || h->batch) return PE_EINVAL;
   const SysDesc &d = h->sys[0];
   if (d.N != d.n) return PE_EINVAL;
+  if (h->qd && P > 0 && pe::newton_qd_needs_scratch(d.n)) {  // double-double systems of the solve
+    const size_t np = static_cast<size_t>(d.n) * static_cast<size_t>(h->max_points);
+    int r;
+    if ((r = ensure(h->nt_Jdd, 32 * np * d.n)) || (r = ensure(h->nt_fdd, 32 * np))) return r;
+  }
   int rc = polyeval_eval(h, points, P, out_f, out_J, stream);
   if (rc != PE_OK || P == 0) return rc;
   pe::NewtonParams np{};
@@ -947,7 +955,11 @@ int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, void *o
   np.f = static_cast<double *>(out_f);
   np.x = static_cast<double *>(points);
   np.norms = norms;
-  if (pe::launch_newton(h->dd, np, static_cast<cudaStream_t>(stream)) != cudaSuccess) return PE_ECUDA;
+  np.Jdd = static_cast<double *>(h->nt_Jdd.p);
+  np.fdd = static_cast<double *>(h->nt_fdd.p);
+  const cudaError_t le = h->qd ? pe::launch_newton_qd(np, static_cast<cudaStream_t>(stream))
+                               : pe::launch_newton(h->dd, np, static_cast<cudaStream_t>(stream));
+  if (le != cudaSuccess) return PE_ECUDA;
   h->kernels_launched++;
   return PE_OK;
 }
@@ -1091,8 +1103,6 @@ bool trackable(const polyeval *h) {
     if (g < 1) return false;
   return true;
 }
-
-int ensure(DeviceBuf &b, size_t bytes) { return b.bytes >= bytes ? PE_OK : b.alloc(bytes); }
 
 int upload_degrees(polyeval *h) {
   if (h->deg_dev.p) return PE_OK;

@@ -96,8 +96,11 @@ struct NewtonParams {
   double *f;        // [n][P] f on entry, dx on return
   double *x;        // [n][P] points, updated in place
   double *norms;    // [P][2] (|f|_inf, |dx|_inf) or nullptr
+  double *Jdd, *fdd;  // quad-double handles: double-double copies of the systems when not staged in shared memory
 };
 cudaError_t launch_newton(bool dd, const NewtonParams &p, cudaStream_t s);
+cudaError_t launch_newton_qd(const NewtonParams &p, cudaStream_t s);
+bool newton_qd_needs_scratch(int n);
 
 // The paper's three-kernel design (three_kernel.cu), complex double-double.
 struct PaperParams {

@@ -416,17 +416,19 @@ __device__ __forceinline__ Mag mag_from_u64(unsigned long long v) {
   return r;
 }
 
-// x0 + x1 + x2 + x3 for any four finite doubles (overlapping, unnormalised
-// or of mixed signs), as sign and magnitude with the leading bit of the
-// largest part at position 250.  Bits below position 0 are dropped (at most 4
-// units of 2^-250 relative to the largest part).
-__device__ __forceinline__ Comp comp_from_qd(const double x[4]) {
-  uint32_t s[4];
-  unsigned long long M[4];
-  int X[4];
+// x0 + ... + x_{NP-1} for any NP <= 8 finite doubles (overlapping,
+// unnormalised or of mixed signs), as sign and magnitude with the leading bit
+// of the largest part at position 250.  Bits below position 0 are dropped (at
+// most NP units of 2^-250 relative to the largest part).
+template <int NP>
+__device__ __forceinline__ Comp comp_from_parts(const double x[NP]) {
+  static_assert(NP >= 1 && NP <= 8, "the sum must stay below 2^255");
+  uint32_t s[NP];
+  unsigned long long M[NP];
+  int X[NP];
   int top = INT32_MIN;
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
+  for (int i = 0; i < NP; i++) {
     wide::split_double(x[i], s[i], M[i], X[i]);
     if (M[i]) top = max(top, X[i] + 63 - __clzll(static_cast<long long>(M[i])));
   }
@@ -434,7 +436,7 @@ __device__ __forceinline__ Comp comp_from_qd(const double x[4]) {
   const int base = top - 250;  // exponent of bit 0
   Mag acc = zero_mag();        // two's complement
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
+  for (int i = 0; i < NP; i++) {
     if (!M[i]) continue;
     const int pos = X[i] - base;  // position of the significand's bit 0
     const Mag v = pos >= 0 ? shl(mag_from_u64(M[i]), pos) : shr(mag_from_u64(M[i]), -pos);
@@ -446,6 +448,8 @@ __device__ __forceinline__ Comp comp_from_qd(const double x[4]) {
   neg_if(acc, neg);
   return Comp{acc, neg & kSignBit, base};
 }
+
+__device__ __forceinline__ Comp comp_from_qd(const double x[4]) { return comp_from_parts<4>(x); }
 
 // A complex quad-double (re0..re3, im0..im3) as a normalised full value.
 __device__ __forceinline__ WF wf_from_cqd(const double *v) {
@@ -704,6 +708,16 @@ __device__ __forceinline__ void acc_to_qd(const Acc &a, double out[4]) {
     }
     s ^= round ? kSignBit : 0u;
   }
+}
+
+// The sum of NP doubles rounded to a normalised quad-double (exact to about
+// 2^-218 of the largest part, then the rounding of acc_to_qd).
+template <int NP>
+__device__ __forceinline__ void parts_to_qd(const double x[NP], double out[4]) {
+  const Comp c = comp_from_parts<NP>(x);
+  Acc a = acc_zero();
+  acc_add(a, WV{c.m, c.s, c.e});
+  acc_to_qd(a, out);
 }
 
 }  // namespace qd

@@ -132,3 +132,34 @@ def normwise_vs(a, b, S):
     with np.errstate(divide="ignore", invalid="ignore"):
         r = np.where(zero, 0.0, d / np.where(zero, 1.0, S))
     return float(np.max(r)) if r.size else 0.0
+
+
+def square_system(seed, n, m, kmax, emax):
+    """A square system of n polynomials in n variables: a constant term (which
+    keeps the Jacobian generic) and m random monomials each."""
+    import synth
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    polys = []
+    for _p in range(n):
+        mons = [([], [])]
+        for _t in range(m):
+            k = int(rng.integers(1, kmax + 1))
+            pos = sorted(rng.choice(n, size=k, replace=False).tolist())
+            mons.append((pos, rng.integers(1, emax + 1, size=k).tolist()))
+        polys.append(mons)
+    return synth.from_monomials(n, polys, synth.random_cdd(rng, n * (m + 1)))
+
+
+def fr_parts(v):
+    """A complex double-double [4] or quad-double [8] as an exact pair of
+    Fractions (re, im)."""
+    from fractions import Fraction
+
+    w = len(v) // 2
+    return (sum((Fraction(float(a)) for a in v[:w]), Fraction(0)),
+            sum((Fraction(float(a)) for a in v[w:]), Fraction(0)))
+
+
+def cabs(z):
+    return abs(complex(float(z[0]), float(z[1])))

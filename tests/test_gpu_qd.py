@@ -307,15 +307,10 @@ def test_qd_config5_sampled():
     check_exact(s, pts, f, J, points_idx=[2047], polys=[127])
 
 
-def test_qd_rejects_newton_and_paper_kernels():
+def test_qd_rejects_paper_kernels():
     import paper_1201_0499_gb300 as pkg
 
     s = random_system(480, n=4, N=4, m=3, kmin=3, kmax=3, emax=2)
-    ev = pkg.PolyEval(s, pkg.PE_QD_INT, max_points=4)
-    x = to_device(synth.widen_qd(np.random.Generator(np.random.PCG64(481)), synth.points(482, 4, 4)))
-    with pytest.raises(pkg.PolyEvalError) as e:
-        ev.newton(x)
-    assert e.value.code == pkg.PE_EINVAL
     with pytest.raises(pkg.PolyEvalError) as e:
         pkg.PolyEval(s, pkg.PE_QD_INT, max_points=4, flags=pkg.PE_PAPER_KERNELS)
     assert e.value.code == pkg.PE_EINVAL

@@ -15,7 +15,7 @@ import synth
 from oracle import exact as E
 from oracle import newton as N
 
-from _util import PRECS, pe_precision, to_device, widen
+from _util import PRECS, cabs, fr_parts as fr_dd, pe_precision, square_system, to_device, widen
 
 pytestmark = pytest.mark.gpu
 
@@ -28,29 +28,6 @@ def _cuda():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     torch.cuda.set_device(0)
-
-
-def square_system(seed, n, m, kmax, emax):
-    rng = np.random.Generator(np.random.PCG64(seed))
-    polys = []
-    for _p in range(n):
-        mons = [([], [])]  # a constant term keeps the Jacobian generic
-        for _t in range(m):
-            k = int(rng.integers(1, kmax + 1))
-            pos = sorted(rng.choice(n, size=k, replace=False).tolist())
-            mons.append((pos, rng.integers(1, emax + 1, size=k).tolist()))
-        polys.append(mons)
-    return synth.from_monomials(n, polys, synth.random_cdd(rng, n * (m + 1)))
-
-
-def fr_dd(v):
-    from fractions import Fraction
-
-    return (Fraction(v[0]) + Fraction(v[1]), Fraction(v[2]) + Fraction(v[3]))
-
-
-def cabs(z):
-    return abs(complex(float(z[0]), float(z[1])))
 
 
 def run_newton(system, pts, prec):
