@@ -343,8 +343,10 @@ def track_leg(pkg, torch):
         st, _t, it = ev.track(x)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+        # iterations of the batch (each one evaluation of f and J at every
+        # running path, the batch compacted as paths end)
         out[name] = {"ms": el * 1e3, "paths_per_s": B / el, "iterations": it,
-                     "evals_per_s": it * B / el, "success": int((st == 1).sum().item())}
+                     "success": int((st == 1).sum().item())}
     lo, hi = hs["f64"], hs["ddint"]
     prm_lo, prm_hi = pkg.polyeval_track_defaults(pkg.PE_F64), pkg.polyeval_track_defaults(pkg.PE_DD)
     status = torch.empty(B, dtype=torch.int32, device="cuda")

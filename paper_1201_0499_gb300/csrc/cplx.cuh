@@ -36,6 +36,7 @@ struct CDD {
                normalize(add(a.im, negate_if(b.im, 0x8000000000000000ULL)))};
   }
   __device__ double abs_hi() const { return sqrt(re.h * re.h + im.h * im.h); }
+  __device__ double norm2_hi() const { return __fma_rn(re.h, re.h, __dmul_rn(im.h, im.h)); }
   __device__ CDD neg() const { return CDD{negate_if(re, 0x8000000000000000ULL), negate_if(im, 0x8000000000000000ULL)}; }
   // x * y, renormalised
   __device__ static CDD mul(const CDD &x, const CDD &y) {
@@ -76,6 +77,7 @@ struct C64 {
   __device__ static C64 scale(const C64 &x, double k) { return C64{__dmul_rn(x.re, k), __dmul_rn(x.im, k)}; }
   __device__ static C64 sub(const C64 &a, const C64 &b) { return C64{__dsub_rn(a.re, b.re), __dsub_rn(a.im, b.im)}; }
   __device__ double abs_hi() const { return sqrt(re * re + im * im); }
+  __device__ double norm2_hi() const { return __fma_rn(re, re, __dmul_rn(im, im)); }
   __device__ C64 neg() const { return C64{-re, -im}; }
   __device__ static C64 mul(const C64 &x, const C64 &y) {
     return C64{__fma_rn(x.re, y.re, -__dmul_rn(x.im, y.im)), __fma_rn(x.re, y.im, __dmul_rn(x.im, y.re))};

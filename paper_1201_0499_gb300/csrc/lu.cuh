@@ -90,7 +90,7 @@ __device__ bool lu_solve(const V &v, const Lanes<S> g) {
     double best = -1.0;
     int piv = n;
     for (int i = k + lane; i < n; i += S) {
-      const double m = C::load(v.Jel(i, k)).abs_hi();
+      const double m = C::load(v.Jel(i, k)).norm2_hi();  // the modulus squared: same order, no square root
       if (m > best) {
         best = m;
         piv = i;
@@ -127,19 +127,33 @@ __device__ bool lu_solve(const V &v, const Lanes<S> g) {
       C::sub_mul(C::load(v.bel(i)), l, bk).store(v.bel(i));
     }
     g.sync();
-    // trailing update: lanes over the columns j > k
-    for (int j = k + 1 + lane; j < n; j += S) {
-      const C u = C::load(v.Jel(k, j));
-      for (int i = k + 1; i < n; i++) C::sub_mul(C::load(v.Jel(i, j)), C::load(v.Jel(i, k)), u).store(v.Jel(i, j));
+    // trailing update: the lanes over the w x w elements (i, j > k) in row
+    // order, so that all S lanes work until w^2 < S (lanes over the columns
+    // alone would leave S - w idle at every step)
+    const int w = n - k - 1;
+    if (w > 0) {
+      int i = k + 1 + lane / w, j = k + 1 + lane % w;
+      const int di = S / w, dj = S % w;
+      for (int e = lane; e < w * w; e += S) {
+        C::sub_mul(C::load(v.Jel(i, j)), C::load(v.Jel(i, k)), C::load(v.Jel(k, j))).store(v.Jel(i, j));
+        i += di;
+        j += dj;
+        if (j >= n) {
+          j -= w;
+          i++;
+        }
+      }
     }
     g.sync();
   }
-  // back substitution, y overwrites b
+  // back substitution, y overwrites b, by columns: x_i = y_i / U_ii (every
+  // lane, which costs the FP64 pipe no more than one), then the lanes over
+  // the rows r < i take x_i out of y_r
   for (int i = n - 1; i >= 0; i--) {
-    C s = C::zero();
-    for (int j = i + 1 + lane; j < n; j += S) s = C::sub_mul(s, C::load(v.Jel(i, j)), C::load(v.bel(j)));
-    for (int d = S / 2; d > 0; d >>= 1) s = C::add2(s, s.shfl_xor(g.mask, d));
-    if (lane == 0) C::mul(C::add2(C::load(v.bel(i)), s).finish(), C::recip(C::load(v.Jel(i, i)))).store(v.bel(i));
+    const C xi = C::mul(C::load(v.bel(i)), C::recip(C::load(v.Jel(i, i))));
+    g.sync();
+    if (lane == 0) xi.store(v.bel(i));
+    for (int r = lane; r < i; r += S) C::sub_mul(C::load(v.bel(r)), C::load(v.Jel(r, i)), xi).store(v.bel(r));
     g.sync();
   }
   return false;
