@@ -66,15 +66,23 @@ def solve(A, b):
     return x
 
 
-def newton_step(system, pts, q):
-    """Exact (f, J, dx, x1) at point q of ``pts`` (float64 [n, P, 4]) for a
-    square system: f and J as complex Fraction pairs (f[i], J[i][j])."""
+def f_and_J(system, pts, q):
+    """Exact f and J at point q of ``pts`` (float64 [n, P, 4] or [n, P, 8])
+    of a square system, as complex Fraction pairs (f[i], J[i][j])."""
     n = system.n_vars
     if system.n_polys != n:
         raise ValueError("Newton's method needs a square system")
     fe, Je = E.evaluate_point(system, pts, q)
     f = [fr(fe[i]) for i in range(n)]
     J = [[fr(Je[i].get(j, E.ZERO)) for j in range(n)] for i in range(n)]
+    return f, J
+
+
+def newton_step(system, pts, q):
+    """Exact (f, J, dx, x1) at point q of ``pts`` (float64 [n, P, 4] or
+    [n, P, 8]) for a square system: f and J as in ``f_and_J``."""
+    n = system.n_vars
+    f, J = f_and_J(system, pts, q)
     dx = solve(J, [c_sub(ZERO, fi) for fi in f])
     x0 = [fr(E.cx_from_dd(pts[v, q])) for v in range(n)]
     return f, J, dx, [c_add(x0[i], dx[i]) for i in range(n)]

@@ -73,7 +73,7 @@ def test_qd_newton_step_against_exact(n):
     assert np.all(dx[..., [2, 3, 6, 7]] == 0.0) and np.all(lu[..., [2, 3, 6, 7]] == 0.0)
     assert_normalised(x1)
     for q in (0, 7, P - 1):
-        f, J, _dx_exact, _x1_exact = N.newton_step(s, pts, q)
+        f, J = N.f_and_J(s, pts, q)
         g = [fr_parts(dx[i, q]) for i in range(n)]
         # dx solves the leading parts of J and f in double-double: its
         # backward error against the exact J and f is that of the solve
@@ -136,3 +136,31 @@ def test_qd_newton_converges_to_quad_double_accuracy():
             err = max(err, cabs(N.c_sub(fr_parts(x[i, q]), fr_parts(root[i, 0]))))
     assert err < 1e-58, err
     assert_normalised(x)
+
+
+def test_qd_newton_singular_point_and_empty_batch():
+    """A point where the Jacobian is exactly zero (x = 0 on x_i^2 + c_i) is
+    left unchanged with dx = 0 and a NaN step norm; its neighbour in the
+    batch still takes its step.  An empty batch is a no-op."""
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+
+    rng = np.random.Generator(np.random.PCG64(720))
+    n = 3
+    polys = [[([i], [2]), ([], [])] for i in range(n)]
+    s = synth.from_monomials(n, polys, synth.random_cdd(rng, 2 * n)).to_qd(721)
+    pts = synth.widen_qd(rng, synth.points(722, n, 2))
+    pts[:, 0, :] = 0.0
+    x1, dx, _lu, norms = newton_qd(s, pts)
+    assert np.all(x1[:, 0] == 0.0) and np.all(dx[:, 0] == 0.0)
+    assert np.isnan(norms[0][0, 1]) and norms[0][1, 1] > 0.0
+    f, J, _dx, _x1 = N.newton_step(s, pts, 1)
+    for i in range(n):
+        want = N.c_add(fr_parts(pts[i, 1]), N.c_div(N.c_sub(N.ZERO, f[i]), J[i][i]))
+        assert cabs(N.c_sub(fr_parts(x1[i, 1]), want)) <= 1e-28 * cabs(want)
+    ev = pkg.PolyEval(s, pkg.PE_QD_INT, max_points=4)
+    x = torch.empty((n, 0, 8), dtype=torch.float64, device="cuda")
+    ev.newton(x)
+    torch.cuda.synchronize()
+    assert ev.status() == pkg.PE_OK
