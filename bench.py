@@ -674,7 +674,10 @@ def main():
                          "fp64_issue_frac": issue_rate / (SMS * DFMA_PER_SM_CLK * sm_max * 1e6),
                          "paper_method_equiv_tflops": (nominal_flops / (kern_avg_ms * 1e-3) / 1e12
                                                        if nominal_flops else None)},
-            "fp64_path": {"evals_per_s": job_throughput(world, P, ms64), "ms_per_step": ms64},
+            "fp64_path": {"evals_per_s": job_throughput(world, P, ms64), "ms_per_step": ms64,
+                          # FP64 instructions of the step's main kernel over the whole step time
+                          "fp64_issue_frac": (wl.cost_per_launch("f64")[0] / (ms64 * 1e-3)
+                                              / (SMS * DFMA_PER_SM_CLK * sm_max * 1e6))},
             "dd_fp64_time_ratio": (ms_per_step if prim == "dd" else legs["dd"]) / ms64,
             ("int_pipe_path" if other == "ddint" else "fp64_dd_path"): {
                 "evals_per_s": job_throughput(world, P, legs[other]), "ms_per_step": legs[other],

@@ -82,15 +82,19 @@ __device__ void track_path(const TrackParams &p, int64_t q, const G grp, double 
   const double tt = predict ? s.t : (s.phase == kPhaseEnd ? 1.0 : s.t1);
   const C a = C::scale(gamma, 1.0 - tt);  // gamma (1 - t)
   const L al = convert<L>(a);
-  for (int i = 0; i < n; i++) {
-    for (int j = lane; j < n; j += G::size) {
-      L e = L::scale(convert<L>(C::load(g.Jel(i, j))), tt);
-      if (j == i) {
-        const L xi = convert<L>(C::load(Xel(p.x, i)));
-        const int d = p.deg[i];
-        e = L::add2(e, L::mul(al, L::scale(cpow(xi, d - 1), static_cast<double>(d)))).finish();
-      }
-      e.store(Ael(i, j));
+  for (int e = lane, i = lane / n, j = lane % n; e < n * n; e += G::size) {  // the n^2 entries over the lanes
+    L v = L::scale(convert<L>(C::load(g.Jel(i, j))), tt);
+    if (j == i) {
+      const L xi = convert<L>(C::load(Xel(p.x, i)));
+      const int d = p.deg[i];
+      v = L::add2(v, L::mul(al, L::scale(cpow(xi, d - 1), static_cast<double>(d)))).finish();
+    }
+    v.store(Ael(i, j));
+    i += G::size / n;
+    j += G::size % n;
+    if (j >= n) {
+      j -= n;
+      i++;
     }
   }
   for (int i = lane; i < n; i += G::size) {
@@ -279,6 +283,19 @@ __global__ void scatter_status(const int32_t *src, int32_t *dst, const int64_t *
 }
 
 namespace {
+constexpr int kTrackWarpsLatency = 152 * 8;
+
+// Lanes per path: as many as the system needs (lanes_for), doubled while
+// the batch would leave fewer than 8 warps per SM: the step is a chain of
+// dependent FP64 operations, latency bound in small batches (late in a run,
+// when most paths have ended), and the LU's element-wise updates spread
+// over the extra lanes.
+int track_lanes(int n, int64_t P) {
+  int S = lanes_for(n);
+  while (S < 32 && P * S < static_cast<int64_t>(kTrackWarpsLatency) * 32) S *= 2;
+  return S;
+}
+
 unsigned grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -313,7 +330,7 @@ cudaError_t launch_track_segments(const TrackParams &p, cudaStream_t s) {
 
 template <class C, class L>
 cudaError_t launch_track_step_t(const TrackParams &p, cudaStream_t s) {
-  switch (lanes_for(p.n)) {
+  switch (track_lanes(p.n, p.P)) {
     case 4: return launch_track_segments<C, L, 4>(p, s);
     case 8: return launch_track_segments<C, L, 8>(p, s);
     case 16: return launch_track_segments<C, L, 16>(p, s);
