@@ -53,7 +53,10 @@ __host__ __device__ constexpr size_t smem_lu_bytes(int n) {
   return static_cast<size_t>(n) * (n + 1) * C::kDoubles * sizeof(double);
 }
 constexpr size_t kSmemLuMax = 16 * 1024;
-constexpr int kLuBlock = 128;  // threads per block of the segment kernels
+// Threads per block of the segment kernels: one warp, so that a batch of a
+// few warps per SM spreads evenly over the 152 SMs (with 4-warp blocks, 1024
+// points at 32 lanes made 256 blocks: 2 on most SMs, 1 on the rest).
+constexpr int kLuBlock = 32;
 
 // The lanes that work on one point: S consecutive lanes of a warp (S a power
 // of two, 4 .. 32) and the mask of their segment.  A warp holds 32 / S points,
