@@ -15,6 +15,10 @@ constexpr int kWarpsPerBlockMax = 4;
 // its monomial groups per warp in bits 27..29 (groups > 1 for the last,
 // partial tile of a system with double-double or double arithmetic).
 constexpr int kTileBits = 27;
+// Streaming-multiprocessor count of a GB300 (two dies of 76): the grids of
+// the grid-stride kernels are capped at a whole number of blocks per SM.
+// Launches whose balance depends on it query the device instead.
+constexpr int kSms = 152;
 
 // One compiled system inside a handle.  Offsets are in complex elements of
 // the handle's precision.

@@ -327,7 +327,7 @@ cudaError_t launch_combine(bool dd, double *out_f, double *out_J, const double *
     const int64_t comps = dd ? doubles / 2 : doubles;
     if (comps <= 0) continue;
     int64_t blocks = (comps + threads - 1) / threads;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > kSms * 64) blocks = kSms * 64;
     if (dd)
       combine_kernel<ArithDD><<<static_cast<unsigned>(blocks), threads, 0, s>>>(out, scr, comps, doubles, chunks);
     else
@@ -342,7 +342,7 @@ cudaError_t launch_powers(bool dd, const PowerParams &p, cudaStream_t s) {
   if (p.total <= 0) return cudaSuccess;
   const int threads = 256;
   int64_t blocks = (p.total + threads - 1) / threads;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > kSms * 64) blocks = kSms * 64;
   if (dd)
     powers_kernel<ArithDD><<<static_cast<unsigned>(blocks), threads, 0, s>>>(p);
   else

@@ -214,7 +214,7 @@ __global__ void finalize_qd(double *out_f, double *out_J, const double *scratch_
 cudaError_t convert_coef_qd(const double *coef_qd, uint32_t *coef_blk, int64_t M, cudaStream_t s) {
   if (M <= 0) return cudaSuccess;
   int64_t blocks = (M + 127) / 128;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > kSms * 32) blocks = kSms * 32;
   convert_coef_qd_kernel<<<static_cast<unsigned>(blocks), 128, 0, s>>>(coef_qd, coef_blk, M);
   return cudaGetLastError();
 }
@@ -222,7 +222,7 @@ cudaError_t convert_coef_qd(const double *coef_qd, uint32_t *coef_blk, int64_t M
 cudaError_t launch_powers_qd(const PowerParams &p, cudaStream_t s) {
   if (p.total <= 0) return cudaSuccess;
   int64_t blocks = (p.total + 127) / 128;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > kSms * 32) blocks = kSms * 32;
   powers_qd<<<static_cast<unsigned>(blocks), 128, 0, s>>>(p);
   return cudaGetLastError();
 }
@@ -246,7 +246,7 @@ cudaError_t launch_finalize_qd(double *out_f, double *out_J, const double *scrat
   const int64_t total = f_components + J_components;
   if (total <= 0) return cudaSuccess;
   int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > kSms * 16) blocks = kSms * 16;
   finalize_qd<<<static_cast<unsigned>(blocks), 256, 0, s>>>(out_f, out_J, scratch_f, scratch_J, f_components,
                                                             J_components, chunks);
   return cudaGetLastError();

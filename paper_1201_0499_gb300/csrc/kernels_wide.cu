@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kWarpsPerBlockMax * 32) main_wide(const MainPa
 cudaError_t convert_coef_wide(const double *coef_dd, uint32_t *coef_wide, int64_t M, cudaStream_t s) {
   if (M <= 0) return cudaSuccess;
   int64_t blocks = (M + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > kSms * 64) blocks = kSms * 64;
   convert_coef_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(coef_dd, coef_wide, M);
   return cudaGetLastError();
 }
@@ -211,7 +211,7 @@ cudaError_t convert_coef_wide(const double *coef_dd, uint32_t *coef_wide, int64_
 cudaError_t launch_powers_wide(const PowerParams &p, cudaStream_t s) {
   if (p.total <= 0) return cudaSuccess;
   int64_t blocks = (p.total + 127) / 128;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > kSms * 64) blocks = kSms * 64;
   powers_wide<<<static_cast<unsigned>(blocks), 128, 0, s>>>(p);
   return cudaGetLastError();
 }

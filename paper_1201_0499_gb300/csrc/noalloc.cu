@@ -29,6 +29,7 @@
 #include <mutex>
 
 #include "dd.cuh"
+#include "internal.h"
 #include "polyeval.h"
 
 namespace pe {
@@ -264,7 +265,7 @@ extern "C" PE_API int polyeval_eval_noalloc(const pe_system *dev_sys, int32_t ma
   if (max_exp > 2) {
     const int64_t total = static_cast<int64_t>(p.n) * P;
     int64_t blocks = (total + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > pe::kSms * 64) blocks = pe::kSms * 64;
     powers<<<static_cast<unsigned>(blocks), 256, 0, s>>>(p);
     if (cudaGetLastError() != cudaSuccess) return PE_ECUDA;
   }

@@ -283,7 +283,7 @@ __global__ void scatter_status(const int32_t *src, int32_t *dst, const int64_t *
 }
 
 namespace {
-constexpr int kTrackWarpsLatency = 152 * 8;
+constexpr int kTrackWarpsLatency = kSms * 8;
 
 // Lanes per path: as many as the system needs (lanes_for), doubled while
 // the batch would leave fewer than 8 warps per SM: the step is a chain of
@@ -299,7 +299,7 @@ int track_lanes(int n, int64_t P) {
 unsigned grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
-  if (b > 152 * 32) b = 152 * 32;
+  if (b > kSms * 32) b = kSms * 32;
   return static_cast<unsigned>(b);
 }
 }  // namespace
