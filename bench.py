@@ -564,16 +564,17 @@ def main():
         legs[leg] = max_over_ranks(timed_loop(leg, kl) / kl, dist)
     ms64 = legs["f64"]
 
-    # Newton step (evaluation + LU solve per point + update) with the primary precision
-    newton = None
-    if args.config != 4:
-        ev_p = wl.ev[prim]
-        x0 = wl.bufs["dd"][0].clone()
+    def newton_leg(prec, ms_eval):
+        """Newton steps from the same start (x restored before each, outside
+        the events); the solve's share is the step time less the evaluation's."""
+        ev_p = wl.ev[prec]
+        xb, fb, Jb = wl.bufs[buf_fmt(prec)]
+        x0 = xb.clone()
         xn = x0.clone()
-        dx = torch.empty_like(wl.bufs["dd"][1])
-        lu = torch.empty_like(wl.bufs["dd"][2])
+        dx = torch.empty_like(fb)
+        lu = torch.empty_like(Jb)
         nrm = torch.empty((P, 2), dtype=torch.float64, device=dev)
-        for _ in range(args.warmup):
+        for _ in range(max(args.warmup, 1)):  # the first quad-double call at n > 22 allocates its scratch
             xn.copy_(x0)
             pkg.polyeval_newton(ev_p.handle, xn, P, dx, lu, nrm, stream)
         kn = max(min(args.steps, 50), 3)
@@ -586,10 +587,18 @@ def main():
             pkg.polyeval_newton(ev_p.handle, xn, P, dx, lu, nrm, stream)
             stops[i].record(stream)
         torch.cuda.synchronize()
-        ms_newton = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, stops)) / kn, dist)
-        newton = {"ms_per_step": ms_newton, "solve_ms": ms_newton - ms_per_step,
-                  "points_per_s": job_throughput(world, P, ms_newton),
-                  "what": "f, J, LU with partial pivoting per point, x += dx (polyeval_newton)"}
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, stops)) / kn, dist)
+        return {"ms_per_step": ms, "solve_ms": ms - ms_eval, "points_per_s": job_throughput(world, P, ms)}
+
+    # Newton step (evaluation + LU solve per point + update) with the primary
+    # precision, and with quad-double (quad-double f and J, double-double solve)
+    newton = None
+    if args.config != 4:
+        newton = newton_leg(prim, ms_per_step)
+        newton["what"] = "f, J, LU with partial pivoting per point, x += dx (polyeval_newton)"
+        newton["qd"] = newton_leg("qd", legs["qd"])
+        newton["qd"]["what"] = ("quad-double f and J, LU in double-double from their leading parts, x + dx "
+                                "rounded to quad-double")
 
     # the paper's three-kernel design on the same batch (double-double), for comparison
     paper = None
