@@ -42,8 +42,8 @@ SMS = 152
 DFMA_PER_SM_CLK = 2  # nominal FP64 FMA lanes per SM per clock on GB300
 # DRAM bytes (read + write) of one main-kernel launch on this workload (two monomial chunks,
 # one wave), from the ncu capture summarised in profiles/main_kernel_dd_n32_m64_k9_p1024.md:
-# 5.44 MB read + 69.49 MB written. Set to None when the kernel changes.
-MAIN_KERNEL_DRAM_BYTES = 5_440_000 + 69_487_872
+# 5.45 MB read + 70.14 MB written. Set to None when the kernel changes.
+MAIN_KERNEL_DRAM_BYTES = 5_449_984 + 70_139_648
 
 
 def env_dist():

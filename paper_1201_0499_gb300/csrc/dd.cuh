@@ -142,6 +142,17 @@ __device__ __forceinline__ dd recip(dd d) {
   return normalize(dd{q, __dmul_rn(q, e)});
 }
 
+// The double equal to an integer 1 <= a < 2^31, assembled from a's bits on
+// the integer pipe (biased exponent 1023 + e for a's leading one at bit e,
+// the bits below it as the fraction): a conversion instruction would take a
+// slot of the FP64 pipe, the bound of the evaluation kernels.
+__device__ __forceinline__ double int_as_double(int a) {
+  const unsigned u = static_cast<unsigned>(a);
+  const int e = 31 - __clz(u);
+  const unsigned long long frac = (static_cast<unsigned long long>(u) << (52 - e)) & 0x000FFFFFFFFFFFFFULL;
+  return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(1023 + e) << 52) | frac));
+}
+
 __device__ __forceinline__ dd negate_if(dd x, unsigned long long sign_mask) {
   return dd{__longlong_as_double(__double_as_longlong(x.h) ^ static_cast<long long>(sign_mask)),
             __longlong_as_double(__double_as_longlong(x.l) ^ static_cast<long long>(sign_mask))};

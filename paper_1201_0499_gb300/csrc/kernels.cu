@@ -113,7 +113,7 @@ __device__ void process_item(const MainParams &kp, const Item &it, typename A::V
     const int vl = static_cast<int>(wl & 0xffffu), al = static_cast<int>(wl >> 16);
     const Full xl = A::load_full(xel(vl));
     f = A::f_add(f, mul_x<A, false>(Pc, xl, sgn, kFull));
-    accumulate<A>(jel(vl), c, valid, al == 1 ? Pc : A::mul_int(Pc, static_cast<double>(al)));
+    accumulate<A>(jel(vl), c, valid, al == 1 ? Pc : A::mul_int(Pc, int_as_double(al)));
     // Stage 2, backward: Q = x_{i_{j+2}} ... x_{i_k}; derivative by x_{i_{j+1}} = a_{j+1} slot_j Q
     V Q = A::comp(xl, c);
     renorm = false;
@@ -121,7 +121,7 @@ __device__ void process_item(const MainParams &kp, const Item &it, typename A::V
       const uint32_t w = __ldg(vw + j);
       const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
       const V D = mul_split<A>(smem[j * 32 + lane], Q, c, sgn, kFull);
-      accumulate<A>(jel(v), c, valid, a == 1 ? D : A::mul_int(D, static_cast<double>(a)));
+      accumulate<A>(jel(v), c, valid, a == 1 ? D : A::mul_int(D, int_as_double(a)));
       if (j > 0) Q = chain(Q, A::load_full(xel(v)));
     }
   }
@@ -218,10 +218,10 @@ __device__ void process_item_groups(const MainParams &kp, const Item &it, typena
         for (int j = k - 2; j >= 0; j--) {
           const int a = static_cast<int>(__ldg(vw + j) >> 16);
           const V D = mul_split<A>(smem[j * 32 + lane], Q, c, sgn, pm);
-          smem[j * 32 + lane] = a == 1 ? D : A::mul_int(D, static_cast<double>(a));
+          smem[j * 32 + lane] = a == 1 ? D : A::mul_int(D, int_as_double(a));
           if (j > 0) Q = chain(Q, A::load_full(xel(static_cast<int>(__ldg(vw + j) & 0xffffu))));
         }
-        smem[(k - 1) * 32 + lane] = al == 1 ? Pc : A::mul_int(Pc, static_cast<double>(al));
+        smem[(k - 1) * 32 + lane] = al == 1 ? Pc : A::mul_int(Pc, int_as_double(al));
       }
     }
     __syncwarp();

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(32) evaluate(const Params p) {
     const Cdd xl = load_cdd(xel(vl));
     f = add(f, mul_by(Pc, xl, sgn, false));
     {
-      const dd d = al == 1 ? Pc : scale(Pc, static_cast<double>(al));
+      const dd d = al == 1 ? Pc : scale(Pc, int_as_double(al));
       double2 *acc = reinterpret_cast<double2 *>(jel(vl)) + c;
       const double2 o = *acc;
       const dd s = add(dd{o.x, o.y}, d);
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(32) evaluate(const Params p) {
     for (int j = k - 2; j >= 0; j--) {
       const int v = __ldg(pv + j), a = __ldg(pa + j);
       const dd D = mul_pair(slots[j * 32 + lane], Q, c, sgn);
-      const dd d = a == 1 ? D : scale(D, static_cast<double>(a));
+      const dd d = a == 1 ? D : scale(D, int_as_double(a));
       double2 *acc = reinterpret_cast<double2 *>(jel(v)) + c;
       const double2 o = *acc;
       const dd s = add(dd{o.x, o.y}, d);
