@@ -6,14 +6,15 @@
 // and stores of the elimination into shared-memory accesses.  Used by the
 // Newton step (newton.cu) and the path tracker (track.cu).
 //
-// In elimination step k the lanes of the segment take the columns j > k of
-// the trailing rows (lane j, j + S, ...), the pivot is the row of largest
-// |J[i][k]| (by the leading parts; the smallest index on ties) found by a
+// In elimination step k the pivot is the row of largest |J[i][k]| (by the
+// leading parts, compared squared; the smallest index on ties) found by a
 // segment-wide arg-max, the multipliers are formed by the lanes that own their
-// rows, and the back substitution reduces each row's dot product across the
-// segment.  (One thread per point, each running a whole elimination, was
-// slower at every batch size measured, up to 16384 points of 14 variables:
-// its dependent chains of loads and stores leave the SMs waiting.)
+// rows, and the lanes of the segment share the (n-k-1)^2 elements of the
+// trailing update in row order; the back substitution goes by columns, the
+// lanes taking x_i out of the rows above it.  (One thread per point, each
+// running a whole elimination, was slower at every batch size measured, up
+// to 16384 points of 14 variables: its dependent chains of loads and stores
+// leave the SMs waiting.)
 // On return J holds the factors (unit lower triangle below the diagonal,
 // after the row exchanges) and b the solution y.
 #pragma once
