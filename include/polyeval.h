@@ -379,7 +379,8 @@ PE_API int polyeval_eval_noalloc(const pe_system *dev_sys, int32_t max_k, int32_
  * are the prod d_i points whose coordinates are roots of unity.  Every path
  * is one point of the evaluator's batch; one iteration evaluates F and J_F
  * at all points (polyeval_eval) and then advances each path by one step of
- * its own state machine (one warp per path): Newton corrector at t1
+ * its own state machine (4 to 32 lanes of a warp per path, as n and the
+ * batch size call for): Newton corrector at t1
  * (accepted when max|dx| <= corr_tol max(1, max|x|) within max_corr steps
  * that keep shrinking, else rejected: back to the last accepted point, step
  * size halved, failed below h_min), Euler predictor along the tangent
