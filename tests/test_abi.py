@@ -105,3 +105,55 @@ def test_validate_rejects(pkg):
     assert pkg.polyeval_validate(_mutate(s, poly_ptr=pp)) == E
     mp = s.mono_ptr.copy(); mp[2] = mp[1] - 1
     assert pkg.polyeval_validate(_mutate(s, mono_ptr=mp)) == E
+
+
+C_PROGRAM = r"""
+#include <stdint.h>
+#include <stdio.h>
+#include "polyeval.h"
+
+int main(void) {
+  /* f_0 = x0^2 x1 + 3, f_1 = (1 + 2i) x1 (two variables, two polynomials) */
+  const int64_t poly_ptr[3] = {0, 2, 3};
+  const int64_t mono_ptr[4] = {0, 2, 2, 3};
+  const int32_t pos[3] = {0, 1, 1};
+  int32_t expo[3] = {2, 1, 1};
+  const pe_cdd coef[3] = {{1.0, 0.0, 0.0, 0.0}, {3.0, 0.0, 0.0, 0.0}, {1.0, 0.0, 2.0, 0.0}};
+  pe_system s;
+  s.n_vars = 2;
+  s.n_polys = 2;
+  s.poly_ptr = poly_ptr;
+  s.mono_ptr = mono_ptr;
+  s.pos = pos;
+  s.exp = expo;
+  s.coef = coef;
+  s.coef_qd = NULL;
+  const int good = polyeval_validate(&s, 0);
+  expo[2] = 0; /* exponent < 1 */
+  const int bad = polyeval_validate(&s, 0);
+  polyeval_destroy(NULL); /* NULL-safe */
+  printf("%d %d %s\n", good, bad, polyeval_strerror(bad));
+  return (good == PE_OK && bad == PE_EINVAL) ? 0 : 1;
+}
+"""
+
+
+def test_header_is_c99_and_library_links_from_c(pkg, tmp_path):
+    """A plain C99 program includes the header (warnings are errors), links
+    against the library and calls the host-only entry points."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lib_dir = os.path.join(ROOT, "paper_1201_0499_gb300")
+    src = tmp_path / "abi.c"
+    exe = tmp_path / "abi"
+    src.write_text(C_PROGRAM)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", lib_dir, "-lpolyeval", f"-Wl,-rpath,{lib_dir}"],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.split()[:2] == ["0", str(pkg.PE_EINVAL)]
