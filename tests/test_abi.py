@@ -157,3 +157,19 @@ def test_header_is_c99_and_library_links_from_c(pkg, tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0, out.stdout + out.stderr
     assert out.stdout.split()[:2] == ["0", str(pkg.PE_EINVAL)]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every entry point raises: there is no CPU
+    fallback behind the binding."""
+    import paper_1201_0499_gb300 as pkg
+    from paper_1201_0499_gb300 import _binding
+
+    monkeypatch.setattr(_binding, "_lib", None)
+    monkeypatch.setattr(_binding, "LIB_PATH", str(tmp_path / "libpolyeval.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        pkg.load_library()
+    with pytest.raises(RuntimeError, match="not built"):
+        pkg.polyeval_validate(_small())
+    with pytest.raises(RuntimeError, match="not built"):
+        pkg.PolyEval(_small(), pkg.PE_DD, max_points=4)
