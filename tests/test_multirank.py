@@ -1,6 +1,7 @@
-"""The N > 1 path of bench.py on CPU: two gloo ranks, each with its own batch
+"""bench.py on CPU.  The N > 1 path: two gloo ranks, each with its own batch
 of points (weak scaling, no collective on the data path), timings reduced to
-the slowest rank, throughput counting every rank's points."""
+the slowest rank, throughput counting every rank's points.  The reference arm
+(the oracle on the host cores) and its JSON line."""
 import os
 import socket
 
@@ -54,3 +55,24 @@ def test_single_rank_defaults():
 
     assert bench.max_over_ranks(5.0, None) == 5.0
     assert bench.job_throughput(1, 1024, 2.0) == pytest.approx(512000.0)
+
+
+def test_reference_arm_prints_one_json_line():
+    """`bench.py --impl reference` (the oracle on the host cores, no GPU)
+    prints one JSON line with the bench contract's keys."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1"],
+                         cwd=root, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "evals/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
