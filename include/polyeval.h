@@ -24,6 +24,11 @@
  *   - Streams are passed as `void *` holding a cudaStream_t (NULL = legacy
  *     default stream).  Every eval call is asynchronous on that stream.
  *   - All sizes are element counts unless stated.
+ *   - A handle owns device scratch (power table, monomial-chunk partial sums,
+ *     solver and tracker buffers) that every call on it reuses: calls on one
+ *     handle must not overlap, neither from several host threads nor on
+ *     several streams without ordering between them.  Different handles are
+ *     independent.
  *
  * Data layouts (structure of arrays, point index fastest):
  *   - A complex double-double (pe_cdd) is 4 doubles: re_hi, re_lo, im_hi,
