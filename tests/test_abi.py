@@ -173,3 +173,23 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         pkg.polyeval_validate(_small())
     with pytest.raises(RuntimeError, match="not built"):
         pkg.PolyEval(_small(), pkg.PE_DD, max_points=4)
+
+
+def test_track_defaults_host_only(pkg):
+    """polyeval_track_defaults runs on the host: the documented defaults per
+    precision, and PE_EINVAL for a precision the tracker does not take."""
+    import cmath
+
+    lo, hi = pkg.polyeval_track_defaults(pkg.PE_F64), pkg.polyeval_track_defaults(pkg.PE_DD)
+    for prm in (lo, hi):
+        assert complex(prm.gamma_re, prm.gamma_im) == pytest.approx(cmath.exp(1j), abs=1e-15)
+        assert 0 < prm.h_min < prm.h_init <= prm.h_max <= 1.0
+        assert prm.corr_tol == 1e-6 and prm.max_corr == 3 and prm.succ_grow == 3
+        assert prm.max_iters >= 1 and prm.x_big > 1.0
+    assert hi.end_tol < lo.end_tol and hi.h_min < lo.h_min
+    assert (lo.mixed, hi.mixed) == (0, 1)
+    assert pkg.polyeval_track_defaults(pkg.PE_DD_INT).end_tol == hi.end_tol
+    for bad in (pkg.PE_QD_INT, 99):
+        with pytest.raises(pkg.PolyEvalError) as e:
+            pkg.polyeval_track_defaults(bad)
+        assert e.value.code == pkg.PE_EINVAL
