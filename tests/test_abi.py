@@ -193,3 +193,31 @@ def test_track_defaults_host_only(pkg):
         with pytest.raises(pkg.PolyEvalError) as e:
             pkg.polyeval_track_defaults(bad)
         assert e.value.code == pkg.PE_EINVAL
+
+
+def test_noalloc_argument_checks_before_any_cuda_call(pkg):
+    """polyeval_eval_noalloc checks its arguments on the host before it
+    touches the device: these calls return without a GPU.  The addresses are
+    never dereferenced on these paths (16 is merely aligned, 24 is not)."""
+    def sysd(n=4, N=2, addr=16):
+        return pkg.pe_system(n, N, addr, addr, addr, addr, addr, None)
+
+    def call(s, max_k=4, max_exp=3, points=16, P=8, f=16, J=16):
+        try:
+            pkg.polyeval_eval_noalloc(s, max_k, max_exp, points, P, f, J)
+            return pkg.PE_OK
+        except pkg.PolyEvalError as e:
+            return e.code
+
+    assert call(sysd(), P=0) == pkg.PE_OK                      # nothing to evaluate
+    assert call(sysd(N=0)) == pkg.PE_OK
+    assert call(sysd(n=0)) == pkg.PE_EINVAL                    # no variables
+    assert call(sysd(), P=-1) == pkg.PE_EINVAL
+    assert call(sysd(), max_exp=0) == pkg.PE_EINVAL
+    assert call(sysd(), max_exp=pkg.PE_MAX_EXP + 1) == pkg.PE_ERANGE
+    assert call(sysd(n=pkg.PE_MAX_VARS + 1)) == pkg.PE_ERANGE
+    assert call(sysd(), points=None) == pkg.PE_EINVAL           # null arrays
+    assert call(sysd(addr=0)) == pkg.PE_EINVAL
+    assert call(sysd(), points=24) == pkg.PE_EINVAL             # misaligned
+    assert call(sysd(), f=24) == pkg.PE_EINVAL
+    assert call(sysd(n=64), max_exp=200, P=100000) == pkg.PE_ERANGE  # power table above the static scratch
