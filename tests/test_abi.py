@@ -221,3 +221,46 @@ def test_noalloc_argument_checks_before_any_cuda_call(pkg):
     assert call(sysd(), points=24) == pkg.PE_EINVAL             # misaligned
     assert call(sysd(), f=24) == pkg.PE_EINVAL
     assert call(sysd(n=64), max_exp=200, P=100000) == pkg.PE_ERANGE  # power table above the static scratch
+
+
+def test_null_handle_and_bad_create_arguments_without_a_gpu(pkg):
+    """Every entry point that takes a handle answers PE_EINVAL for a NULL one,
+    and polyeval_create rejects bad arguments before any CUDA call."""
+    import ctypes
+
+    lib = pkg.load_library()
+    N = None
+    calls = {
+        "polyeval_eval": (N, N, 4, N, N, N),
+        "polyeval_eval_host": (N, N, 4, N, N, N),
+        "polyeval_autotune": (N, N, 4, N, N, N, N, N, N),
+        "polyeval_set_launch": (N, 4, 1, 1, 1),
+        "polyeval_newton": (N, N, 4, N, N, N, N),
+        "polyeval_eval_many": (N, N, N, N, N),
+        "polyeval_many_layout": (N, 0, N, N, N),
+        "polyeval_cost": (N, N, N),
+        "polyeval_timing": (N, 1),
+        "polyeval_timing_read": (N, N, N, N),
+        "polyeval_status": (N,),
+        "polyeval_bezout": (N, N, N),
+        "polyeval_start_points": (N, 0, 4, N, N),
+        "polyeval_track": (N, N, N, 4, N, N, N, N),
+        "polyeval_track_adaptive": (N, N, N, N, N, 4, N, N, N),
+    }
+    assert set(calls) | {"polyeval_destroy"} >= {n for n in declared_entry_points()
+                                                  if n not in ("polyeval_validate", "polyeval_create",
+                                                               "polyeval_create_many", "polyeval_strerror",
+                                                               "polyeval_fp64_peak", "polyeval_eval_noalloc",
+                                                               "polyeval_track_defaults")}
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == pkg.PE_EINVAL, name
+    lib.polyeval_destroy(None)
+
+    s = pkg.pe_system()  # all zero: n_vars = 0 is invalid
+    out = ctypes.c_void_p()
+    assert lib.polyeval_create(None, pkg.PE_DD, 0, 4, ctypes.byref(out)) == pkg.PE_EINVAL
+    assert lib.polyeval_create(ctypes.byref(s), pkg.PE_DD, 0, 4, None) == pkg.PE_EINVAL
+    assert lib.polyeval_create(ctypes.byref(s), 77, 0, 4, ctypes.byref(out)) == pkg.PE_EINVAL
+    assert lib.polyeval_create(ctypes.byref(s), pkg.PE_DD, 0, 0, ctypes.byref(out)) == pkg.PE_EINVAL
+    assert lib.polyeval_create(ctypes.byref(s), pkg.PE_DD, 0, 4, ctypes.byref(out)) == pkg.PE_EINVAL  # n_vars 0
+    assert out.value is None
