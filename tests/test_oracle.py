@@ -538,3 +538,39 @@ def test_newton_exact_residual_identity():
             for j in range(3):
                 acc = N.c_add(acc, N.c_mul(J[i][j], dx[j]))
             assert acc == N.ZERO
+
+
+def _newton_pins():
+    return [test_newton_exact_on_linear_system_lands_on_solution, test_newton_exact_univariate_closed_form,
+            test_newton_exact_residual_identity]
+
+
+@pytest.mark.parametrize("mistake", ["negated_step", "transposed_jacobian", "wrong_division", "dropped_pivot_row"])
+def test_newton_planted_mistake_is_caught(mistake, monkeypatch):
+    """A plausible mistake planted in the Newton oracle's solve fails at least
+    one of the Newton pins above."""
+    from oracle import newton as N
+
+    solve, c_div = N.solve, N.c_div
+    if mistake == "negated_step":
+        monkeypatch.setattr(N, "solve", lambda A, b: [(-x[0], -x[1]) for x in solve(A, b)])
+    elif mistake == "transposed_jacobian":
+        monkeypatch.setattr(N, "solve", lambda A, b: solve([list(r) for r in zip(*A)], b))
+    elif mistake == "wrong_division":  # conjugate of the right quotient
+        monkeypatch.setattr(N, "c_div", lambda x, y: (c_div(x, y)[0], -c_div(x, y)[1]))
+    else:  # elimination that skips the last row
+        def partial(A, b):
+            n = len(A)
+            if n == 1:
+                return solve(A, b)
+            x = solve([row[:n - 1] for row in A[:n - 1]], b[:n - 1])
+            return x + [N.ZERO]
+        monkeypatch.setattr(N, "solve", partial)
+    results = []
+    for pin in _newton_pins():
+        try:
+            pin()
+            results.append(True)
+        except AssertionError:
+            results.append(False)
+    assert not all(results), f"{mistake} survived every Newton pin"

@@ -10,6 +10,7 @@ solutions (the Bezout number).
 import itertools
 
 import numpy as np
+import pytest
 
 import synth
 from oracle import exact as E
@@ -109,3 +110,41 @@ def test_no_finite_solutions_paths_do_not_succeed():
                              [[1, 0, 0, 0], [-1, 0, 0, 0], [1, 0, 0, 0], [-2, 0, 0, 0]])
     res = T.solve_system(s, T.Params(max_steps=5000))
     assert all(st != T.SUCCESS for _, st in res)
+
+
+def _track_pins():
+    return [test_univariate_roots_match_numpy, test_decoupled_system_product_set,
+            test_linear_system_matches_numpy_solve, test_start_points_are_roots_of_unity_in_mixed_radix_order]
+
+
+def _mistake(name, monkeypatch):
+    eval_fJ, solve, start = T.eval_fJ, T.solve, T.start_points
+    if name == "jacobian_transposed":
+        def wrong(system, x):
+            F, J = eval_fJ(system, x)
+            return F, [list(r) for r in zip(*J)]
+        monkeypatch.setattr(T, "eval_fJ", wrong)
+    elif name == "dropped_last_term":
+        def wrong(system, x):
+            F, J = eval_fJ(system, x)
+            return [f - (1 if i == len(F) - 1 else 0) for i, f in enumerate(F)], J
+        monkeypatch.setattr(T, "eval_fJ", wrong)
+    elif name == "negated_solution":
+        monkeypatch.setattr(T, "solve", lambda A, b: None if solve(A, b) is None else [-y for y in solve(A, b)])
+    elif name == "start_points_off_the_roots_of_unity":
+        monkeypatch.setattr(T, "start_points", lambda degs: [[1.1 * z for z in x] for x in start(degs)])
+
+
+@pytest.mark.parametrize("name", ["jacobian_transposed", "dropped_last_term", "negated_solution",
+                                  "start_points_off_the_roots_of_unity"])
+def test_planted_mistake_in_the_tracking_oracle_is_caught(name, monkeypatch):
+    """A mistake planted in the tracking oracle fails at least one pin."""
+    _mistake(name, monkeypatch)
+    results = []
+    for pin in _track_pins():
+        try:
+            pin()
+            results.append(True)
+        except AssertionError:
+            results.append(False)
+    assert not all(results), f"{name} survived every pin"
