@@ -218,6 +218,19 @@ PE_API int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out
  * *chunks, *shape and *groups (any may be NULL).  The outputs hold a valid
  * evaluation on return.  Not for use during stream capture.  Errors: those of
  * polyeval_eval.
+ *
+ * Batch handles (polyeval_create_many): pass P = 0 and the batch buffers of
+ * polyeval_eval_many.  The candidates are the monomial chunks of every
+ * (polynomial, tile) item (1, 2, 4, 8, as the handle's chunk scratch allows:
+ * at create a batch handle allocates min(7 copies of all its f and J,
+ * 256 MiB) when that holds at least one copy), the launch shape, and for
+ * PE_DD and PE_F64 the monomial groups of a system's partial last tile
+ * (*groups = 16: a tile of r < 16 points takes the largest G with G r <= 16
+ * groups of 32 / G lanes; *groups = 1: one group, lane pairs past r idle).
+ * The choice is kept for polyeval_eval_many.  Before a change of the
+ * partial-tile groups the call waits for all work on the device and rewrites
+ * the handle's item table.  Errors as for single handles; PE_EINVAL for
+ * P != 0.
  */
 PE_API int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream,
                              int *chunks, int *shape, int *groups);
@@ -230,7 +243,10 @@ PE_API int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void 
  * monomial groups per warp (PE_DD and PE_F64; ignored by the integer-pipe
  * precisions).  0 for any leaves that choice to the built-in heuristic (for
  * groups: the largest G with G P <= 16); all 0 removes the entry.
- * Single-system handles.  Errors: PE_EINVAL.
+ * Batch handles: P = 0; chunks and shape as above for polyeval_eval_many,
+ * groups the most monomial groups of a partial last tile (0 or 16: as many as
+ * fill the warp, the built-in choice); the call waits for all work on the
+ * device when it rewrites the item table.  Errors: PE_EINVAL; PE_ECUDA.
  */
 PE_API int polyeval_set_launch(polyeval_t *h, int64_t P, int chunks, int shape, int groups);
 

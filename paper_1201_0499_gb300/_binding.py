@@ -494,6 +494,13 @@ class PolyEvalMany:
         self.eval_buffers(pts_buf, f_buf, J_buf, stream)
         return self.views(f_buf, J_buf)
 
+    def autotune(self, pts_buf, f_buf, J_buf, stream=None):
+        """Tune the batch launch on the packed buffers; returns (chunks, shape, groups)."""
+        return polyeval_autotune(self.handle, pts_buf, 0, f_buf, J_buf, stream)
+
+    def set_launch(self, chunks: int = 0, shape: int = 0, groups: int = 0):
+        polyeval_set_launch(self.handle, 0, chunks, shape, groups)
+
     def cost(self):
         return polyeval_cost(self.handle)
 

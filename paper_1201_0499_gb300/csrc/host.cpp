@@ -104,6 +104,14 @@ struct polyeval {
     int groups;  // monomial groups per warp (0: built-in choice)
   };
   std::vector<Tuned> tuned;  // launch choices found by polyeval_autotune, per point count
+  // batch handles: the (polynomial, tile) work items in decreasing cost order
+  // with the points of each tile, and the launch of polyeval_eval_many
+  struct BatchTile {
+    int32_t gp, tile, in_tile;
+  };
+  std::vector<BatchTile> btiles;
+  int batch_gcap = pe::kPointsPerWarp;  // most monomial groups a partial tile may take
+  int batch_chunks = 0, batch_mode = 0;  // 0: built-in choice
   // timing of the main kernel
   bool timing = false;
   cudaEvent_t ev[2 * kMaxTimingEvents] = {};
@@ -156,6 +164,30 @@ size_t outputs_bytes(const polyeval *h, int64_t P) {
   const SysDesc &d = h->sys[0];
   return static_cast<size_t>(elem_doubles(h)) * sizeof(double) * static_cast<size_t>(P) *
          (static_cast<size_t>(d.N) + static_cast<size_t>(d.N) * d.n);
+}
+
+// Bytes of one copy of all f and J of a batch handle.
+size_t batch_outputs_bytes(const polyeval *h) {
+  return static_cast<size_t>(elem_doubles(h)) * sizeof(double) *
+         static_cast<size_t>(h->f_total_batch + h->J_total_batch);
+}
+
+// The item table of a batch handle: (global polynomial, tile word) per item
+// in decreasing cost order.  The tile word holds the tile index and log2 of
+// the monomial groups of the item: a partial last tile with r < 16 points
+// spreads them over the largest G <= gcap with G r <= 16 groups (double-double
+// and double kernels; the integer-pipe kernels take one group).
+std::vector<int32_t> batch_item_words(const polyeval *h, int gcap) {
+  std::vector<int32_t> w;
+  w.reserve(h->btiles.size() * 2);
+  for (const polyeval::BatchTile &t : h->btiles) {
+    int lg = 0;
+    if (!block_format(h))
+      while ((2 << lg) * t.in_tile <= pe::kPointsPerWarp && (2 << lg) <= gcap && lg < 4) lg++;
+    w.push_back(t.gp);
+    w.push_back(t.tile | (lg << pe::kTileBits));
+  }
+  return w;
 }
 
 // FP64 instructions and flops per point for one monomial (k variables, n2 of
@@ -631,7 +663,7 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
     int64_t pt = 0, fo = 0, jo = 0, to = 0;
     std::vector<int64_t> prefix{0};
     struct Item {
-      int32_t gp, tile;
+      int32_t gp, tile, in_tile;
       double cost;
     };
     std::vector<Item> items;
@@ -664,11 +696,7 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
         flops += c.poly_flops[gp] * P;
         for (int32_t tl = 0; tl < d.tiles; tl++) {
           const int32_t in_tile = static_cast<int32_t>(std::min<int64_t>(pe::kPointsPerWarp, P - tl * pe::kPointsPerWarp));
-          // a partial last tile spreads its points over monomial groups
-          int lg = 0;
-          if (!block_format(h))
-            while ((2 << lg) * in_tile <= pe::kPointsPerWarp && lg < 4) lg++;
-          items.push_back(Item{gp, tl | (lg << pe::kTileBits), c.poly_ops[gp] * in_tile});
+          items.push_back(Item{gp, tl, in_tile, c.poly_ops[gp] * in_tile});
         }
       }
     }
@@ -677,12 +705,9 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
       return PE_ERANGE;
     }
     std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
-    std::vector<int32_t> it2;
-    it2.reserve(items.size() * 2);
-    for (const Item &it : items) {
-      it2.push_back(it.gp);
-      it2.push_back(it.tile);
-    }
+    h->btiles.reserve(items.size());
+    for (const Item &it : items) h->btiles.push_back(polyeval::BatchTile{it.gp, it.tile, it.in_tile});
+    const std::vector<int32_t> it2 = batch_item_words(h, h->batch_gcap);
     h->n_items_batch = static_cast<int64_t>(items.size());
     h->power_total_batch = prefix.back();
     h->f_total_batch = fo;
@@ -694,6 +719,14 @@ int polyeval_create_many(const pe_system *systems, int32_t count, int precision,
         (rc = h->table.alloc(static_cast<size_t>(to) * table_entry_bytes(h))) != PE_OK) {
       delete h;
       return rc;
+    }
+    {  // scratch for monomial chunks of batches with few work items
+      const size_t per_chunk = batch_outputs_bytes(h);
+      const size_t want = std::min(static_cast<size_t>(kMaxChunks - 1) * per_chunk, kScratchBudget);
+      if (per_chunk > 0 && want >= per_chunk && (rc = h->scratch.alloc(want)) != PE_OK) {
+        delete h;
+        return rc;
+      }
     }
   } catch (const std::bad_alloc &) {
     delete h;
@@ -845,6 +878,136 @@ int eval_single(polyeval *h, const void *points, int64_t P, void *out_f, void *o
   return PE_OK;
 }
 
+// One batch evaluation.  chunks > 0 and mode > 0 force the monomial chunk
+// count and the launch shape (the autotuner); 0 takes the handle's choice,
+// else the built-in one (one chunk; the shape from the item count).
+int eval_many(polyeval *h, const void *points, void *out_f, void *out_J, cudaStream_t s, int chunks, int mode) {
+  if (!h || !h->batch) return PE_EINVAL;
+  if (h->n_items_batch == 0) return PE_OK;
+  if (!points || !out_f || !out_J || !arrays_aligned(points, out_f, out_J)) return PE_EINVAL;
+  if (h->power_total_batch > 0) {
+    pe::PowerParams pp{};
+    pp.sys = static_cast<const SysDesc *>(h->sysd.p);
+    pp.prefix = static_cast<const int64_t *>(h->prefix.p);
+    pp.points = static_cast<const double *>(points);
+    pp.table = static_cast<double *>(h->table.p);
+    pp.total = h->power_total_batch;
+    pp.count = h->count;
+    pp.single_P = -1;
+    if (run_powers(h, pp, s) != PE_OK) return PE_ECUDA;
+  }
+  if (chunks <= 0) chunks = h->batch_chunks;
+  if (mode <= 0) mode = h->batch_mode;
+  const size_t per_chunk = batch_outputs_bytes(h);
+  int C = std::max(1, std::min(chunks, kMaxChunks));
+  C = static_cast<int>(std::min<int64_t>(C, 1 + static_cast<int64_t>(per_chunk ? h->scratch.bytes / per_chunk : 0)));
+  if (h->n_items_batch * C > INT32_MAX) C = 1;  // the work counter is 32-bit
+  const int64_t f_doubles = static_cast<int64_t>(elem_doubles(h)) * h->f_total_batch;
+  const int64_t J_doubles = static_cast<int64_t>(elem_doubles(h)) * h->J_total_batch;
+  pe::MainParams mp = main_params(h);
+  mp.points = static_cast<const double *>(points);
+  mp.out_f = static_cast<double *>(out_f);
+  mp.out_J = static_cast<double *>(out_J);
+  mp.single_P = -1;
+  mp.single_T = 0;
+  mp.n_chunks = C;
+  mp.chunk_f_stride = f_doubles;
+  mp.chunk_J_stride = J_doubles;
+  mp.scratch_f = static_cast<double *>(h->scratch.p);
+  mp.scratch_J = C > 1 ? mp.scratch_f + static_cast<size_t>(C - 1) * f_doubles : nullptr;
+  mp.n_items = h->n_items_batch * C;
+  const int rc = run_main(h, mp, s, std::max(mode, 0));
+  if (rc != PE_OK) return rc;
+  if (h->qd) {  // add the chunks' accumulators, round to quad-double
+    if (pe::launch_finalize_qd(mp.out_f, mp.out_J, mp.scratch_f, mp.scratch_J, 2 * h->f_total_batch,
+                               2 * h->J_total_batch, C, s) != cudaSuccess)
+      return PE_ECUDA;
+    h->kernels_launched++;
+    return PE_OK;
+  }
+  if (C == 1) return PE_OK;
+  if (pe::launch_combine(h->dd, mp.out_f, mp.out_J, mp.scratch_f, mp.scratch_J, f_doubles, J_doubles, C, s) !=
+      cudaSuccess)
+    return PE_ECUDA;
+  h->kernels_launched += 2;  // f and J passes
+  return PE_OK;
+}
+
+// Rewrites the batch item table for a cap on the monomial groups of partial
+// tiles (after the work queued on every stream has finished).
+int set_batch_gcap(polyeval *h, int gcap) {
+  if (gcap == h->batch_gcap) return PE_OK;
+  const std::vector<int32_t> w = batch_item_words(h, gcap);
+  if (cudaDeviceSynchronize() != cudaSuccess) return PE_ECUDA;
+  if (!w.empty() && cudaMemcpy(h->items.p, w.data(), w.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+    return PE_ECUDA;
+  h->batch_gcap = gcap;
+  return PE_OK;
+}
+
+// polyeval_autotune for a batch handle: monomial chunks (as the scratch
+// allows), launch shape, and the cap on monomial groups of partial tiles
+// (1: none; 16: as many as fill the warp).
+int autotune_many(polyeval *h, const void *points, void *out_f, void *out_J, cudaStream_t s, int *chunks, int *shape,
+                  int *groups) {
+  if (!points || !out_f || !out_J || !arrays_aligned(points, out_f, out_J)) return PE_EINVAL;
+  if (h->n_items_batch == 0) return PE_OK;
+  const int64_t capacity = static_cast<int64_t>(h->sms) * h->blocks_per_sm_1;
+  const size_t per_chunk = batch_outputs_bytes(h);
+  const int max_c = per_chunk ? static_cast<int>(std::min<int64_t>(
+                                    kMaxChunks, 1 + static_cast<int64_t>(h->scratch.bytes / per_chunk)))
+                              : 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return PE_ECUDA;
+  }
+  const bool timing = h->timing;
+  h->timing = false;
+  float best = 0.0f;
+  int best_c = 1, best_m = 2, best_g = h->batch_gcap;
+  int rc = PE_OK;
+  // the integer-pipe kernels take one group per item whatever the cap
+  const int caps[2] = {block_format(h) ? 1 : pe::kPointsPerWarp, 1};
+  for (int gi = 0; gi < (block_format(h) ? 1 : 2) && rc == PE_OK; gi++) {
+    rc = set_batch_gcap(h, caps[gi]);
+    for (int C = 1; C <= max_c && rc == PE_OK; C *= 2) {
+      if (h->n_items_batch * C > INT32_MAX) continue;
+      for (int m = 1; m <= 2 && rc == PE_OK; m++) {
+        if (m == 1 && h->n_items_batch * C > capacity) continue;  // one wave only when every item is resident
+        rc = eval_many(h, points, out_f, out_J, s, C, m);  // warm-up
+        if (rc != PE_OK) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) rc = PE_ECUDA;
+        for (int r = 0; r < 3 && rc == PE_OK; r++) rc = eval_many(h, points, out_f, out_J, s, C, m);
+        if (rc == PE_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+          rc = PE_ECUDA;
+        float ms = 0.0f;
+        if (rc == PE_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = PE_ECUDA;
+        if (rc == PE_OK && (best == 0.0f || ms < best)) {
+          best = ms;
+          best_c = C;
+          best_m = m;
+          best_g = caps[gi];
+        }
+      }
+    }
+  }
+  h->timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != PE_OK) return rc;
+  if ((rc = set_batch_gcap(h, best_g)) != PE_OK) return rc;
+  h->batch_chunks = best_c;
+  h->batch_mode = best_m;
+  // leave a valid evaluation with the chosen launch in the outputs
+  if ((rc = eval_many(h, points, out_f, out_J, s, 0, 0)) != PE_OK) return rc;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PE_ECUDA;
+  if (chunks) *chunks = best_c;
+  if (shape) *shape = best_m;
+  if (groups) *groups = best_g;
+  return PE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -859,7 +1022,11 @@ int polyeval_eval(polyeval_t *h, const void *points, int64_t P, void *out_f, voi
 
 int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream,
                       int *chunks, int *shape, int *groups) {
-  if (!h || h->batch || P < 1) return PE_EINVAL;
+  if (h && h->batch) {
+    if (P != 0) return PE_EINVAL;
+    return autotune_many(h, points, out_f, out_J, static_cast<cudaStream_t>(stream), chunks, shape, groups);
+  }
+  if (!h || P < 1) return PE_EINVAL;
   if (P > h->max_points) return PE_ERANGE;
   if (!points || !out_f || !out_J || !arrays_aligned(points, out_f, out_J)) return PE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -926,8 +1093,17 @@ int polyeval_autotune(polyeval_t *h, const void *points, int64_t P, void *out_f,
 
 
 int polyeval_set_launch(polyeval_t *h, int64_t P, int chunks, int shape, int groups) {
-  if (!h || h->batch || P < 1 || chunks < 0 || chunks > kMaxChunks || shape < 0 || shape > 2) return PE_EINVAL;
+  if (!h || chunks < 0 || chunks > kMaxChunks || shape < 0 || shape > 2) return PE_EINVAL;
   if (groups != 0 && groups != 1 && groups != 2 && groups != 4 && groups != 8 && groups != 16) return PE_EINVAL;
+  if (h->batch) {
+    if (P != 0) return PE_EINVAL;
+    const int rc = set_batch_gcap(h, groups > 0 ? groups : pe::kPointsPerWarp);
+    if (rc != PE_OK) return rc;
+    h->batch_chunks = chunks;
+    h->batch_mode = shape;
+    return PE_OK;
+  }
+  if (P < 1) return PE_EINVAL;
   for (auto it = h->tuned.begin(); it != h->tuned.end(); ++it)
     if (it->P == P) {
       h->tuned.erase(it);
@@ -965,36 +1141,7 @@ int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, void *o
 }
 
 int polyeval_eval_many(polyeval_t *h, const void *points, void *out_f, void *out_J, void *stream) {
-  if (!h || !h->batch) return PE_EINVAL;
-  if (h->n_items_batch == 0) return PE_OK;
-  if (!points || !out_f || !out_J || !arrays_aligned(points, out_f, out_J)) return PE_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (h->power_total_batch > 0) {
-    pe::PowerParams pp{};
-    pp.sys = static_cast<const SysDesc *>(h->sysd.p);
-    pp.prefix = static_cast<const int64_t *>(h->prefix.p);
-    pp.points = static_cast<const double *>(points);
-    pp.table = static_cast<double *>(h->table.p);
-    pp.total = h->power_total_batch;
-    pp.count = h->count;
-    pp.single_P = -1;
-    if (run_powers(h, pp, s) != PE_OK) return PE_ECUDA;
-  }
-  pe::MainParams mp = main_params(h);
-  mp.points = static_cast<const double *>(points);
-  mp.out_f = static_cast<double *>(out_f);
-  mp.out_J = static_cast<double *>(out_J);
-  mp.single_P = -1;
-  mp.single_T = 0;
-  mp.n_chunks = 1;
-  mp.n_items = h->n_items_batch;
-  const int rc = run_main(h, mp, s);
-  if (rc != PE_OK || !h->qd) return rc;
-  if (pe::launch_finalize_qd(mp.out_f, mp.out_J, nullptr, nullptr, 2 * h->f_total_batch, 2 * h->J_total_batch, 1, s) !=
-      cudaSuccess)
-    return PE_ECUDA;
-  h->kernels_launched++;
-  return PE_OK;
+  return eval_many(h, points, out_f, out_J, static_cast<cudaStream_t>(stream), 0, 0);
 }
 
 int polyeval_eval_host(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream) {

@@ -5,7 +5,8 @@
 // (C = 1 unless the call has too few (polynomial, tile) pairs to fill the
 // GPU).  Chunk 0 writes f and J into the outputs; chunk c > 0 into scratch
 // copy c-1 of the same layout, which a combine kernel adds afterwards.  A
-// batch handle has one item per (polynomial, tile) from its item table.
+// batch handle has C items per (polynomial, tile) entry of its item table,
+// chunked the same way.
 #pragma once
 
 #include <cstdint>
@@ -36,7 +37,10 @@ __device__ __forceinline__ bool decode_item(const MainParams &kp, unsigned item,
     it.P = kp.single_P;
     it.groups = kp.groups;
   } else {
-    const int2 x = kp.items[item];
+    const unsigned C = static_cast<unsigned>(kp.n_chunks);
+    const unsigned rest = item / C;
+    chunk = static_cast<int>(item - rest * C);
+    const int2 x = kp.items[rest];
     it.gp = x.x;
     it.groups = 1 << ((x.y >> kTileBits) & 7);
     it.tile = (x.y & ((1 << kTileBits) - 1)) * it.groups;  // in tiles of 16 / groups points
