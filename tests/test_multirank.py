@@ -28,7 +28,7 @@ def _worker(rank, world, port, out):
         r, w, local = bench.env_dist()
         ms = 3.0 + r  # the ranks' step times differ
         slowest = bench.max_over_ranks(ms, dist)
-        seed = bench.rank_points_seed(r)
+        seed = bench.rank_points_seed(bench.CONFIG_INDEX, r)
         seeds = [None] * w
         dist.all_gather_object(seeds, seed)
         out[rank] = (r, w, local, slowest, bench.job_throughput(w, 1024, slowest), tuple(seeds))
@@ -65,7 +65,8 @@ def test_reference_arm_prints_one_json_line():
     import sys
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1"],
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
+                          "--reference-points", "2"],
                          cwd=root, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
@@ -76,3 +77,4 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["points_per_step"] == 2 and "n=128" in d["config"]["workload"]
