@@ -363,8 +363,9 @@ PE_API int polyeval_status(polyeval_t *h);
  * let this library call cudaMalloc, and so cannot use polyeval_create.  This
  * entry point allocates nothing: the caller passes the system, the points
  * and the outputs in its own device memory, and the only scratch -- the
- * table of powers of Section 3.1 -- lives in a static 16 MiB device array
- * that every GPU loading the library holds until the process exits.
+ * table of powers x^2 .. x^(d-1) of every variable at every point -- lives
+ * in a static 16 MiB device array that every GPU loading the library holds
+ * until the process exits.
  *
  *   dev_sys   host struct in the pe_system format whose pointer fields
  *             (poly_ptr, mono_ptr, pos, exp, coef) are DEVICE pointers; the
@@ -378,9 +379,15 @@ PE_API int polyeval_status(polyeval_t *h);
  * 16 MiB array (524288 of them), else PE_ERANGE; PE_EINVAL for null pointers
  * or negative sizes.  A monomial breaking max_k, max_exp or 0 <= pos < n is
  * skipped and f of its polynomial is written as NaN.
+ * Each one-warp block takes (max_k - 1) * 512 bytes of shared memory (one
+ * forward-product slot per variable and lane), so the bound sets how many
+ * warps share an SM: pass the smallest max_k that holds (max_k = 256 takes
+ * about 130 KB, one warp per SM; 32 takes 16 KB).
  * The first call on a device looks up the array's device address (and sets
- * the kernel's shared-memory limit) with that device current; make that
- * first call before any stream capture.  Every call uses the same array:
+ * the kernel's shared-memory limit) with that device current and keeps both
+ * for the life of the process; make that first call before any stream
+ * capture.  A device reset (cudaDeviceReset) after it is not supported: the
+ * kept address and limit belong to the context the reset destroys.  Every call uses the same array:
  * each call writes all the table entries it reads before reading them, so
  * nothing has to start at zero, but calls that overlap on the GPU (other
  * streams or host threads) race on it.
@@ -428,7 +435,7 @@ typedef struct {
 #define PE_PATH_RUNNING 0       /* max_iters reached first                         */
 #define PE_PATH_SUCCESS 1       /* reached t = 1 and converged there               */
 #define PE_PATH_FAILED 2        /* step size fell below h_min                      */
-#define PE_PATH_DIVERGED 3      /* max|x| exceeded x_big                           */
+#define PE_PATH_DIVERGED 3      /* max|x| exceeded x_big, or x or dx not finite    */
 #define PE_PATH_END_NOT_CONVERGED 4 /* at t = 1 Newton did not reach end_tol (singular or ill-conditioned end point) */
 
 /* Default tracking parameters for a precision (PE_DD, PE_DD_INT or PE_F64):

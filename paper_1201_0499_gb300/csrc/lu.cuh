@@ -59,6 +59,11 @@ constexpr size_t kSmemLuMax = 16 * 1024;
 // points at 32 lanes made 256 blocks: 2 on most SMs, 1 on the rest).
 constexpr int kLuBlock = 32;
 
+// max(a, b) that keeps a NaN (fmax drops it): a norm taken over values one of
+// which is NaN is NaN, so a path or a Newton step that produced a NaN (an
+// overflow, inf - inf) cannot pass a tolerance test on the other entries.
+__device__ __forceinline__ double nan_max(double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); }
+
 // The lanes that work on one point: S consecutive lanes of a warp (S a power
 // of two, 4 .. 32) and the mask of their segment.  A warp holds 32 / S points,
 // so that a small system does not leave most lanes idle: on GB300 an FP64
@@ -76,7 +81,7 @@ struct Lanes {
     return Lanes{t & (S - 1), m};
   }
   __device__ double max(double v) const {
-    for (int d = S / 2; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, d));
+    for (int d = S / 2; d > 0; d >>= 1) v = nan_max(v, __shfl_xor_sync(mask, v, d));
     return v;
   }
   __device__ void sync() const { __syncwarp(mask); }

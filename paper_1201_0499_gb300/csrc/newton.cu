@@ -40,7 +40,7 @@ __global__ void newton_lu(const NewtonParams p) {
   double fnorm = 0.0;
   for (int i = lane; i < n; i += S) {
     const C fi = C::load(gv.bel(i));
-    fnorm = fmax(fnorm, fi.abs_hi());
+    fnorm = nan_max(fnorm, fi.abs_hi());
     fi.neg().store(bel(i));
   }
   fnorm = g.max(fnorm);
@@ -56,7 +56,7 @@ __global__ void newton_lu(const NewtonParams p) {
     // x <- x + dx; dx to f
     for (int i = lane; i < n; i += S) {
       const C dx = C::load(bel(i));
-      dxnorm = fmax(dxnorm, dx.abs_hi());
+      dxnorm = nan_max(dxnorm, dx.abs_hi());
       dx.store(gv.bel(i));
       C::add2(C::load(Xel(i)), dx).finish().store(Xel(i));
     }
@@ -138,7 +138,7 @@ __global__ void newton_qd(const NewtonParams p) {
   double fnorm = 0.0;
   for (int i = lane; i < n; i += S) {
     const CDD fi = lead(fq(i));
-    fnorm = fmax(fnorm, fi.abs_hi());
+    fnorm = nan_max(fnorm, fi.abs_hi());
     fi.neg().store(bel(i));
   }
   fnorm = g.max(fnorm);
@@ -154,7 +154,7 @@ __global__ void newton_qd(const NewtonParams p) {
       continue;
     }
     const CDD dx = CDD::load(bel(i));
-    dxnorm = fmax(dxnorm, dx.abs_hi());
+    dxnorm = nan_max(dxnorm, dx.abs_hi());
     double *x = xq(i);
     for (int c = 0; c < 2; c++) {  // x_c + dx_c, six parts summed exactly, rounded to four
       const dd d = c == 0 ? dx.re : dx.im;

@@ -147,14 +147,14 @@ __device__ void track_path(const TrackParams &p, int64_t q, const G grp, double 
       const C dx = convert<C>(L::load(bel(i)));
       const C x1 = C::add2(C::load(Xel(p.x, i)), dx).finish();
       x1.store(Xel(p.x, i));
-      dxn = fmax(dxn, dx.abs_hi());
-      xn = fmax(xn, x1.abs_hi());
+      dxn = nan_max(dxn, dx.abs_hi());
+      xn = nan_max(xn, x1.abs_hi());
     }
     dxn = grp.max(dxn);
     xn = grp.max(xn);
     s.iter++;
     const double scale = fmax(1.0, xn);
-    if (!(xn <= p.x_big)) {
+    if (!(xn <= p.x_big) || !(dxn == dxn) || isinf(xn)) {  // beyond x_big, or not finite
       s.status = kPathDiverged;
     } else if (s.phase == kPhaseEnd) {
       if (dxn <= p.end_tol * scale)

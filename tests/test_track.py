@@ -283,6 +283,26 @@ def test_track_half_the_paths_diverge(prec):
 
 
 @pytest.mark.parametrize("prec", ["f64", "dd"])
+def test_track_paths_that_overflow_end_diverged(prec):
+    """x0^2 = 1/4 and 1e307 x1^2 - 1e307 x1^2 + x1 - 1/2 = 0: the two
+    x1^2 terms cancel exactly while they are finite, so F is x1 - 1/2 there,
+    but the total degree is 2 and one path of each x0 root goes to infinity.
+    Past |x1| = 4.3 both terms overflow and F(x) = inf - inf = NaN.  A NaN in
+    one coordinate of a step must not be dropped by the step-size test (a max
+    that skips NaN would accept the step on the finite coordinate and carry
+    the NaN on to a "success"): the two finite solutions succeed with finite
+    coordinates, the two other paths end diverged."""
+    s = synth.from_monomials(2, [[([0], [2]), ([], [])], [([1], [2]), ([1], [2]), ([1], [1]), ([], [])]],
+                             [[1, 0, 0, 0], [-0.25, 0, 0, 0], [1e307, 0, 0, 0], [-1e307, 0, 0, 0],
+                              [1, 0, 0, 0], [-0.5, 0, 0, 0]])
+    z, raw, st, _, _ = run_track(s, prec)
+    ok = st == 1
+    assert int(np.sum(ok)) == 2 and np.all(np.isfinite(z[ok])), (st, z)
+    assert np.all(st[~ok] == 3), st
+    assert match([z[i] for i in np.flatnonzero(ok)], [[0.5, 0.5], [-0.5, 0.5]], 1e-9)
+
+
+@pytest.mark.parametrize("prec", ["f64", "dd"])
 def test_track_double_root_is_not_reported_as_converged(prec):
     """(x - 1)^2 = 0, y^2 = 2: every path ends at a double root in x, where
     Newton's method converges only linearly, so no path may report success;
