@@ -300,13 +300,6 @@ def test_config2_full_batch_f64():
     check_exact_oracle(s64, p64, f, J, F64_TOL, points_idx=[0, 700, 1023], polys=[0, 31])
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_config3_sampled(prec):
-    s, pts = synth.config(3)
-    f, J = run(s, pts, prec)
-    check_exact_oracle(s, pts, f, J, tol(prec), points_idx=[0, 4095], polys=[0, 63], dd=prec != "f64")
-
-
 @pytest.mark.parametrize("prec", ["dd", "ddint"])
 def test_config3_homogeneous_euler_identity(prec):
     """sum_i x_i df_p/dx_i = 24 f_p on the homogeneous variant (degree 24),
@@ -363,23 +356,6 @@ def test_config4_ragged_batch(prec):
         q = int(rng.integers(0, x.shape[1]))
         p = int(rng.integers(0, s.n_polys))
         check_exact_oracle(s, x, f, J, DD_TOL, points_idx=[q], polys=[p])
-
-
-@pytest.mark.parametrize("prec", PRECS)
-def test_config5_large_sampled(prec):
-    import torch
-
-    import oracle
-
-    s, pts = synth.config(5)
-    f, J = run(s, pts, prec)
-    check_exact_oracle(s, pts, f, J, tol(prec), points_idx=[16383], polys=[127], dd=prec != "f64")
-    if prec != "f64":
-        sub = [0, 8191, 16383]
-        Fo, Jo = oracle.dd_eval(s, pts[:, sub].copy(), threads=0)
-        Sf, SJ = scales(s, pts[:, sub])
-        assert normwise_vs(f[:, sub], Fo, Sf) <= DD_TOL
-        assert normwise_vs(J[:, :, sub], Jo, SJ) <= DD_TOL
 
 
 # ----------------------------------------------------------------------------
