@@ -100,6 +100,12 @@ __device__ __forceinline__ void accumulate_dd(double *p, int c, bool valid, dd x
   if (valid) reinterpret_cast<double2 *>(p)[c] = make_double2(s.h, s.l);
 }
 
+// One work item.  Pf: the table value of the next product and the J entry
+// of the next derivative term are read one step ahead, so that their L2 (or
+// DRAM) latency overlaps the current product's carry chains; this holds about
+// 30 more registers per thread, which pays where shared memory already limits
+// the resident warps (large k) and costs occupancy where it does not.
+template <bool Pf>
 __device__ void process_item_wide(const MainParams &kp, const Item &it, uint32_t *slots, int lane) {
   const int gp = it.gp, tile = it.tile, s = it.s, P = it.P;
   const SysDesc sd = kp.sys[s];
@@ -116,6 +122,7 @@ __device__ void process_item_wide(const MainParams &kp, const Item &it, uint32_t
 
   auto tel = [&](int e, int v) { return Tb + ((static_cast<size_t>(e - 1) * n + v) * Pz + qc) * kWideWords; };
   auto jel = [&](int v) { return Jrow + (static_cast<size_t>(v) * Pz + qc) * 4; };
+  auto xw = [&](const uint32_t *vw, int j) { return wide::load_wf(tel(1, static_cast<int>(__ldg(vw + j) & 0xffffu))); };
 
   if (valid)
     for (int v = 0; v < n; v++) reinterpret_cast<double2 *>(jel(v))[c] = make_double2(0.0, 0.0);
@@ -139,37 +146,101 @@ __device__ void process_item_wide(const MainParams &kp, const Item &it, uint32_t
       return r;
     };
     // Stage 1: G = c * prod_{a_j >= 2} x_{i_j}^(a_j - 1)
-    for (int j = 0; j < k; j++) {
-      const uint32_t w = __ldg(vw + j);
-      const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
-      if (a >= 2) G = chain(G, wide::load_wf(tel(a - 1, v)));
+    if constexpr (Pf) {
+      int j = 0;
+      uint32_t w = 0;
+      for (; j < k; j++) {
+        w = __ldg(vw + j);
+        if ((w >> 16) >= 2) break;
+      }
+      WF xa;
+      if (j < k) xa = wide::load_wf(tel(static_cast<int>(w >> 16) - 1, static_cast<int>(w & 0xffffu)));
+      while (j < k) {
+        const WF xc = xa;
+        for (j++; j < k; j++) {
+          w = __ldg(vw + j);
+          if ((w >> 16) >= 2) break;
+        }
+        if (j < k) xa = wide::load_wf(tel(static_cast<int>(w >> 16) - 1, static_cast<int>(w & 0xffffu)));
+        G = chain(G, xc);
+      }
+    } else {
+      for (int j = 0; j < k; j++) {
+        const uint32_t w = __ldg(vw + j);
+        const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
+        if (a >= 2) G = chain(G, wide::load_wf(tel(a - 1, v)));
+      }
     }
     // Stage 2, forward: P_j = G x_{i_1} ... x_{i_j}; every kp.slot_stride-th
     // one is kept (slot j / stride), the others are recomputed below
     const int stride = kp.slot_stride;
     WV Pc = G;
+    WF xf;
+    if constexpr (Pf) xf = xw(vw, 0);
     for (int j = 0; j < k - 1; j++) {
       if (j % stride == 0) store_slot(slots, j / stride, lane, Pc);
-      const int v = static_cast<int>(__ldg(vw + j) & 0xffffu);
-      Pc = chain(Pc, wide::load_wf(tel(1, v)));
+      if constexpr (Pf) {
+        const WF xc = xf;
+        xf = xw(vw, j + 1);  // j + 1 <= k - 1
+        Pc = chain(Pc, xc);
+      } else {
+        Pc = chain(Pc, xw(vw, j));
+      }
     }
     const uint32_t wl = __ldg(vw + k - 1);
     const int vl = static_cast<int>(wl & 0xffffu), al = static_cast<int>(wl >> 16);
-    const WF xl = wide::load_wf(tel(1, vl));
+    WF xl;
+    if constexpr (Pf)
+      xl = xf;  // x_{i_k}
+    else
+      xl = wide::load_wf(tel(1, vl));
     f = add(f, wide::to_dd(wide::mul_x<false>(Pc, xl, c)));  // to_dd takes any leading bit
     accumulate_dd(jel(vl), c, valid, wide::to_dd(al == 1 ? Pc : wide::mul_small(Pc, static_cast<uint32_t>(al))));
-    // Stage 2, backward
+    // Stage 2, backward.  With Pf the J entry of the next term is read one
+    // term ahead: the positions of a monomial are distinct, so it is not the
+    // entry this term writes.
     WV Q = wide::component(xl, c);
     norm = false;
+    WF xb;
+    double2 jb = make_double2(0.0, 0.0);
+    if constexpr (Pf) {
+      if (k >= 2) {
+        const int v0 = static_cast<int>(__ldg(vw + k - 2) & 0xffffu);
+        xb = wide::load_wf(tel(1, v0));
+        jb = reinterpret_cast<const double2 *>(jel(v0))[c];
+      }
+    }
     for (int j = k - 2; j >= 0; j--) {
       const uint32_t w = __ldg(vw + j);
       const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
+      WF xc;        // x_{i_j}
+      double2 jc;   // J[p, i_j]
+      if constexpr (Pf) {
+        xc = xb;
+        jc = jb;
+        if (j > 0) {
+          const int vn = static_cast<int>(__ldg(vw + j - 1) & 0xffffu);
+          xb = wide::load_wf(tel(1, vn));
+          jb = reinterpret_cast<const double2 *>(jel(vn))[c];
+        }
+      }
       WV Pj = load_slot(slots, j / stride, lane);
-      for (int r = j - j % stride; r < j; r++)  // recompute P_j from the kept P_{j - j % stride}
-        Pj = wide::mul_x(Pj, wide::load_wf(tel(1, static_cast<int>(__ldg(vw + r) & 0xffffu))), c);
+      for (int r = j - j % stride; r < j; r++) {  // recompute P_j from the kept P_{j - j % stride}
+        if constexpr (Pf)
+          Pj = wide::mul_x(Pj, r == j - 1 ? xb : xw(vw, r), c);
+        else
+          Pj = wide::mul_x(Pj, xw(vw, r), c);
+      }
       const WV D = wide::mul_pair(Pj, Q, c);
-      accumulate_dd(jel(v), c, valid, wide::to_dd(a == 1 ? D : wide::mul_small(D, static_cast<uint32_t>(a))));
-      if (j > 0) Q = chain(Q, wide::load_wf(tel(1, v)));
+      const dd term = wide::to_dd(a == 1 ? D : wide::mul_small(D, static_cast<uint32_t>(a)));
+      if constexpr (Pf) {
+        const dd sum = add(dd{jc.x, jc.y}, term);
+        if (valid) reinterpret_cast<double2 *>(jel(v))[c] = make_double2(sum.h, sum.l);
+        if (j > 0) Q = chain(Q, xc);
+      } else {
+        accumulate_dd(jel(v), c, valid, term);
+        if (j > 0) Q = chain(Q, wide::load_wf(tel(1, v)));
+      }
     }
   }
   if (valid) {
@@ -185,6 +256,7 @@ __device__ void process_item_wide(const MainParams &kp, const Item &it, uint32_t
   }
 }
 
+template <bool Pf>
 __global__ void __launch_bounds__(kWarpsPerBlockMax * 32) main_wide(const MainParams kp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -196,7 +268,7 @@ __global__ void __launch_bounds__(kWarpsPerBlockMax * 32) main_wide(const MainPa
     if (static_cast<int64_t>(item) >= kp.n_items) break;
     Item it;
     if (!decode_item(kp, item, lane, it)) continue;
-    process_item_wide(kp, it, slots, lane);
+    process_item_wide<Pf>(kp, it, slots, lane);
   }
 }
 
@@ -217,16 +289,25 @@ cudaError_t launch_powers_wide(const PowerParams &p, cudaStream_t s) {
 }
 
 cudaError_t prepare_main_wide(size_t smem_bytes) {
-  return cudaFuncSetAttribute(main_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
+  const cudaError_t e =
+      cudaFuncSetAttribute(main_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(main_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
 }
 
-cudaError_t main_wide_occupancy(int warps_per_block, size_t smem_bytes, int *blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_wide, warps_per_block * 32, smem_bytes);
+cudaError_t main_wide_occupancy(bool prefetch, int warps_per_block, size_t smem_bytes, int *blocks_per_sm) {
+  return prefetch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_wide<true>, warps_per_block * 32,
+                                                                  smem_bytes)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_wide<false>, warps_per_block * 32,
+                                                                  smem_bytes);
 }
 
 cudaError_t launch_main_wide(const MainParams &p, int warps_per_block, size_t smem_bytes, int grid, cudaStream_t s) {
   if (p.n_items <= 0) return cudaSuccess;
-  main_wide<<<grid, warps_per_block * 32, smem_bytes, s>>>(p);
+  if (p.prefetch)
+    main_wide<true><<<grid, warps_per_block * 32, smem_bytes, s>>>(p);
+  else
+    main_wide<false><<<grid, warps_per_block * 32, smem_bytes, s>>>(p);
   return cudaGetLastError();
 }
 
