@@ -24,10 +24,12 @@ constexpr int kMaxTimingEvents = 256;
 // in at most kScratchBudget bytes of handle-owned scratch.
 constexpr int kMaxChunks = 8;
 constexpr size_t kScratchBudget = size_t{256} << 20;
-// Integer path: above this many prefix slots per lane a warp's slots no longer
-// leave room for 16 warps per SM, and only every second slot is stored.
-constexpr int kWideSlotsFull = 20;
-// Quad-double path: the same with its 36-byte slots (16 warps per SM).
+// Integer double-double path: the largest slot stride tried (every
+// stride-th forward product kept in shared memory, the others recomputed).
+constexpr int kWideMaxStride = 3;
+// Quad-double path: above this many prefix slots per lane a warp's 36-byte
+// slots no longer leave room for 16 warps per SM, and only every second slot
+// is stored.
 constexpr int kQdSlotsFull = 12;
 
 struct DeviceBuf {
@@ -74,7 +76,7 @@ struct polyeval {
   int32_t n_polys_total = 0;
   int32_t kmax = 0, kslots = 1;
   int32_t slot_stride = 1;  // integer path: keep every slot_stride-th forward product
-  bool wide_prefetch = false;  // integer-pipe paths: the kernel that reads one step ahead
+  bool wide_prefetch = false;  // integer double-double path: the kernel that reads one step ahead
   int warps_per_block = pe::kWarpsPerBlockMax;
   size_t smem_bytes = 0;
   int blocks_per_sm = 1, sms = 1;
@@ -356,7 +358,7 @@ int finish_handle(polyeval *h, Compiled &c) {
   // forward products k - 1 per monomial; the grouped kernel also parks the k
   // derivative terms in the slots
   h->kslots = block_format(h) ? std::max(c.kmax - 1, 1) : std::max(c.kmax, 1);
-  if ((h->wide && h->kslots > kWideSlotsFull) || (h->qd && h->kslots > kQdSlotsFull)) {
+  if (h->qd && h->kslots > kQdSlotsFull) {
     // keep every second forward product (the others are recomputed in the
     // backward pass) so that enough warps fit in shared memory
     h->slot_stride = 2;
@@ -367,30 +369,50 @@ int finish_handle(polyeval *h, Compiled &c) {
   if (cudaGetDevice(&dev) != cudaSuccess) return PE_ECUDA;
   if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PE_ECUDA;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return PE_ECUDA;
+  auto block_warps = [&](size_t pw) {
+    int w = pe::kWarpsPerBlockMax;
+    while (w > 1 && pw * w > static_cast<size_t>(optin)) w /= 2;
+    return w;
+  };
+  if (h->wide) {
+    // The integer kernel is bound by the latency of its carry chains, so
+    // resident warps pay for recomputed products: take the slot stride
+    // (1 .. kWideMaxStride) that leaves the most warps resident, the smallest
+    // among equals.  Measured on GB300: n = 128, k = 32: stride 3 (32 warps
+    // per SM) 4.43 K evaluations/s against 4.07 K with stride 2 (20 warps) and
+    // 2.58 K with stride 1; n = 64, k = 16: stride 2 76.1 K, stride 1 71.5 K.
+    if (pe::prepare_main_wide(static_cast<size_t>(optin)) != cudaSuccess) return PE_ECUDA;
+    const int base = std::max(c.kmax - 1, 1);
+    int best_w = -1;
+    for (int st = 1; st <= kWideMaxStride; st++) {
+      const int ks = (base + st - 1) / st;
+      const size_t pw = static_cast<size_t>(ks) * 32 * pe::kWideSlotBytes;
+      const int wpb = block_warps(pw);
+      if (pw * wpb > static_cast<size_t>(optin)) continue;
+      int blocks = 0;
+      if (pe::main_wide_occupancy(false, wpb, pw * wpb, &blocks) != cudaSuccess) return PE_ECUDA;
+      if (blocks * wpb > best_w) {
+        best_w = blocks * wpb;
+        h->slot_stride = st;
+        h->kslots = ks;
+      }
+    }
+    if (best_w < 0) return PE_ERANGE;
+  }
   const size_t per_warp = static_cast<size_t>(h->kslots) * 32 *
                          (h->qd ? pe::kQdSlotBytes : h->wide ? pe::kWideSlotBytes : (h->dd ? 16 : 8));
-  h->warps_per_block = pe::kWarpsPerBlockMax;
-  while (h->warps_per_block > 1 && per_warp * h->warps_per_block > static_cast<size_t>(optin)) h->warps_per_block /= 2;
+  h->warps_per_block = block_warps(per_warp);
   if (per_warp * h->warps_per_block > static_cast<size_t>(optin)) return PE_ERANGE;
   h->smem_bytes = per_warp * h->warps_per_block;
   h->smem_per_warp = per_warp;
   if (h->qd) {
     if (pe::prepare_main_qd(static_cast<size_t>(optin)) != cudaSuccess) return PE_ECUDA;
-    int plain = 0, ahead = 0;  // as for the double-double integer kernel below (n = 128, k = 32: +10 %)
-    if (pe::main_qd_occupancy(false, h->warps_per_block, h->smem_bytes, &plain) != cudaSuccess ||
-        pe::main_qd_occupancy(true, h->warps_per_block, h->smem_bytes, &ahead) != cudaSuccess)
-      return PE_ECUDA;
-    h->wide_prefetch = ahead >= plain;
-    h->blocks_per_sm = h->wide_prefetch ? ahead : plain;
-    if (pe::main_qd_occupancy(h->wide_prefetch, 1, per_warp, &h->blocks_per_sm_1) != cudaSuccess) return PE_ECUDA;
+    if (pe::main_qd_occupancy(h->warps_per_block, h->smem_bytes, &h->blocks_per_sm) != cudaSuccess) return PE_ECUDA;
+    if (pe::main_qd_occupancy(1, per_warp, &h->blocks_per_sm_1) != cudaSuccess) return PE_ECUDA;
   } else if (h->wide) {
-    if (pe::prepare_main_wide(static_cast<size_t>(optin)) != cudaSuccess) return PE_ECUDA;
     // The kernel that reads one step ahead holds more registers: take it when
-    // it keeps as many resident warps as the other (shared memory, not
-    // registers, limits residency for large k).  Measured on GB300: n = 128,
-    // k = 32: 4.09 K against 3.45 K evaluations/s; n = 64, k = 16: 68.4 K
-    // against 65.3 K; at n = 32, k = 9, where it would cost a third of the
-    // warps, it was 10 % slower.
+    // it keeps as many resident warps as the other (where shared memory, not
+    // registers, limits residency; with the stride chosen above that is rare).
     int plain = 0, ahead = 0;
     if (pe::main_wide_occupancy(false, h->warps_per_block, h->smem_bytes, &plain) != cudaSuccess ||
         pe::main_wide_occupancy(true, h->warps_per_block, h->smem_bytes, &ahead) != cudaSuccess)

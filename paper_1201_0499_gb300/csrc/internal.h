@@ -55,7 +55,7 @@ struct MainParams {
   int32_t groups;           // monomial groups per warp (1, 2, 4, 8, 16; double-double and double only)
   int32_t kslots;           // prefix-product slots per lane (max k - 1, at least 1)
   int32_t slot_stride;      // integer path: every slot_stride-th forward product is kept
-  int32_t prefetch;         // integer-pipe paths: the kernel that reads table values and J entries one step ahead
+  int32_t prefetch;         // integer double-double path: the kernel that reads table values and J entries one step ahead
   int32_t n_polys_total;
   int32_t n_chunks;         // single handle: chunks per polynomial's monomials (>= 1)
   int64_t chunk_f_stride;   // doubles between scratch copies of f
@@ -143,7 +143,7 @@ constexpr int kQdSlotBytes = 9 * 4;  // per lane and prefix-product slot
 cudaError_t convert_coef_qd(const double *coef_qd, uint32_t *coef_blk, int64_t M, cudaStream_t s);
 cudaError_t launch_powers_qd(const PowerParams &p, cudaStream_t s);
 cudaError_t prepare_main_qd(size_t smem_bytes);
-cudaError_t main_qd_occupancy(bool prefetch, int warps_per_block, size_t smem_bytes, int *blocks_per_sm);
+cudaError_t main_qd_occupancy(int warps_per_block, size_t smem_bytes, int *blocks_per_sm);
 cudaError_t launch_main_qd(const MainParams &p, int warps_per_block, size_t smem_bytes, int grid, cudaStream_t s);
 // Sums the accumulators of `chunks` copies (the outputs, then scratch copies
 // 1 .. chunks-1 of the same layout) and rounds them to quad-double in the

@@ -107,11 +107,6 @@ __device__ __forceinline__ void accumulate(double *entry, int c, bool valid, con
   if (valid) qd::store_acc(p, a);
 }
 
-// One work item.  Pf: the table value of the next product and the
-// accumulator of the next derivative term are read one step ahead (their L2
-// latency overlaps the current product), at the cost of about 30 more
-// registers per thread; taken where shared memory limits the resident warps.
-template <bool Pf>
 __device__ void process_item_qd(const MainParams &kp, const Item &it, uint32_t *slots, int lane) {
   const int gp = it.gp, tile = it.tile, s = it.s, P = it.P;
   const SysDesc sd = kp.sys[s];
@@ -128,7 +123,6 @@ __device__ void process_item_qd(const MainParams &kp, const Item &it, uint32_t *
 
   auto tel = [&](int e, int v) { return Tb + ((static_cast<size_t>(e - 1) * n + v) * Pz + qc) * kQdWords; };
   auto jel = [&](int v) { return Jrow + (static_cast<size_t>(v) * Pz + qc) * kQdDoubles; };
-  auto xw = [&](const uint32_t *vw, int j) { return qd::load_wf(tel(1, static_cast<int>(__ldg(vw + j) & 0xffffu))); };
 
   if (valid)
     for (int v = 0; v < n; v++) qd::store_acc(jel(v) + 4 * c, qd::acc_zero());
@@ -145,106 +139,41 @@ __device__ void process_item_qd(const MainParams &kp, const Item &it, uint32_t *
     }
     const uint32_t *vw = kp.var + vb;
     // Stage 1: G = c * prod_{a_j >= 2} x_{i_j}^(a_j - 1)
-    if constexpr (Pf) {
-      int j = 0;
-      uint32_t w = 0;
-      for (; j < k; j++) {
-        w = __ldg(vw + j);
-        if ((w >> 16) >= 2) break;
-      }
-      WF xa;
-      if (j < k) xa = qd::load_wf(tel(static_cast<int>(w >> 16) - 1, static_cast<int>(w & 0xffffu)));
-      while (j < k) {
-        const WF xc = xa;
-        for (j++; j < k; j++) {
-          w = __ldg(vw + j);
-          if ((w >> 16) >= 2) break;
-        }
-        if (j < k) xa = qd::load_wf(tel(static_cast<int>(w >> 16) - 1, static_cast<int>(w & 0xffffu)));
-        G = qd::mul_x(G, xc, c);
-      }
-    } else {
-      for (int j = 0; j < k; j++) {
-        const uint32_t w = __ldg(vw + j);
-        const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
-        if (a >= 2) G = qd::mul_x(G, qd::load_wf(tel(a - 1, v)), c);
-      }
+    for (int j = 0; j < k; j++) {
+      const uint32_t w = __ldg(vw + j);
+      const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
+      if (a >= 2) G = qd::mul_x(G, qd::load_wf(tel(a - 1, v)), c);
     }
     // Stage 2, forward: P_j = G x_{i_1} ... x_{i_j}; every kp.slot_stride-th
     // one is kept (slot j / stride), the others are recomputed below
     const int stride = kp.slot_stride;
     WV Pc = G;
-    WF xf;
-    if constexpr (Pf) xf = xw(vw, 0);
     for (int j = 0; j < k - 1; j++) {
       if (j % stride == 0) store_slot(slots, j / stride, lane, Pc);
-      if constexpr (Pf) {
-        const WF xc = xf;
-        xf = xw(vw, j + 1);  // j + 1 <= k - 1
-        Pc = qd::mul_x(Pc, xc, c);
-      } else {
-        Pc = qd::mul_x(Pc, xw(vw, j), c);
-      }
+      const int v = static_cast<int>(__ldg(vw + j) & 0xffffu);
+      Pc = qd::mul_x(Pc, qd::load_wf(tel(1, v)), c);
     }
     const uint32_t wl = __ldg(vw + k - 1);
     const int vl = static_cast<int>(wl & 0xffffu), al = static_cast<int>(wl >> 16);
-    WF xl;
-    if constexpr (Pf)
-      xl = xf;  // x_{i_k}
-    else
-      xl = qd::load_wf(tel(1, vl));
+    const WF xl = qd::load_wf(tel(1, vl));
     qd::acc_add(f, qd::mul_x(Pc, xl, c));
     accumulate(jel(vl), c, valid, al == 1 ? Pc : qd::mul_small(Pc, static_cast<uint32_t>(al)));
-    // Stage 2, backward.  With Pf the accumulator of the next term is read
-    // one term ahead: the positions of a monomial are distinct, so it is not
-    // the entry this term writes.
+    // Stage 2, backward
     WV Q = qd::component(xl, c);
-    WF xb;
-    Acc jb = qd::acc_zero();
-    if constexpr (Pf) {
-      if (k >= 2) {
-        const int v0 = static_cast<int>(__ldg(vw + k - 2) & 0xffffu);
-        xb = qd::load_wf(tel(1, v0));
-        jb = qd::load_acc(jel(v0) + 4 * c);
-      }
-    }
     for (int j = k - 2; j >= 0; j--) {
       const uint32_t w = __ldg(vw + j);
       const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
-      WF xc;   // x_{i_j}
-      Acc jc;  // accumulator of J[p, i_j]
-      if constexpr (Pf) {
-        xc = xb;
-        jc = jb;
-        if (j > 0) {
-          const int vn = static_cast<int>(__ldg(vw + j - 1) & 0xffffu);
-          xb = qd::load_wf(tel(1, vn));
-          jb = qd::load_acc(jel(vn) + 4 * c);
-        }
-      }
       WV Pj = load_slot(slots, j / stride, lane);
-      for (int r = j - j % stride; r < j; r++) {  // recompute P_j from the kept P_{j - j % stride}
-        if constexpr (Pf)
-          Pj = qd::mul_x(Pj, r == j - 1 ? xb : xw(vw, r), c);
-        else
-          Pj = qd::mul_x(Pj, xw(vw, r), c);
-      }
+      for (int r = j - j % stride; r < j; r++)  // recompute P_j from the kept P_{j - j % stride}
+        Pj = qd::mul_x(Pj, qd::load_wf(tel(1, static_cast<int>(__ldg(vw + r) & 0xffffu))), c);
       const WV D = qd::mul_pair(Pj, Q, c);
-      const WV term = a == 1 ? D : qd::mul_small(D, static_cast<uint32_t>(a));
-      if constexpr (Pf) {
-        qd::acc_add(jc, term);
-        if (valid) qd::store_acc(jel(v) + 4 * c, jc);
-        if (j > 0) Q = qd::mul_x(Q, xc, c);
-      } else {
-        accumulate(jel(v), c, valid, term);
-        if (j > 0) Q = qd::mul_x(Q, qd::load_wf(tel(1, v)), c);
-      }
+      accumulate(jel(v), c, valid, a == 1 ? D : qd::mul_small(D, static_cast<uint32_t>(a)));
+      if (j > 0) Q = qd::mul_x(Q, qd::load_wf(tel(1, v)), c);
     }
   }
   if (valid) qd::store_acc(it.f_base + (static_cast<size_t>(sd.f_off) + static_cast<size_t>(pl) * Pz + q) * kQdDoubles + 4 * c, f);
 }
 
-template <bool Pf>
 __global__ void __launch_bounds__(kWarpsPerBlockMax * 32) main_qd(const MainParams kp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -256,7 +185,7 @@ __global__ void __launch_bounds__(kWarpsPerBlockMax * 32) main_qd(const MainPara
     if (static_cast<int64_t>(item) >= kp.n_items) break;
     Item it;
     if (!decode_item(kp, item, lane, it)) continue;
-    process_item_qd<Pf>(kp, it, slots, lane);
+    process_item_qd(kp, it, slots, lane);
   }
 }
 
@@ -299,25 +228,16 @@ cudaError_t launch_powers_qd(const PowerParams &p, cudaStream_t s) {
 }
 
 cudaError_t prepare_main_qd(size_t smem_bytes) {
-  const cudaError_t e =
-      cudaFuncSetAttribute(main_qd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(main_qd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
+  return cudaFuncSetAttribute(main_qd, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
 }
 
-cudaError_t main_qd_occupancy(bool prefetch, int warps_per_block, size_t smem_bytes, int *blocks_per_sm) {
-  return prefetch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_qd<true>, warps_per_block * 32,
-                                                                  smem_bytes)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_qd<false>, warps_per_block * 32,
-                                                                  smem_bytes);
+cudaError_t main_qd_occupancy(int warps_per_block, size_t smem_bytes, int *blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_qd, warps_per_block * 32, smem_bytes);
 }
 
 cudaError_t launch_main_qd(const MainParams &p, int warps_per_block, size_t smem_bytes, int grid, cudaStream_t s) {
   if (p.n_items <= 0) return cudaSuccess;
-  if (p.prefetch)
-    main_qd<true><<<grid, warps_per_block * 32, smem_bytes, s>>>(p);
-  else
-    main_qd<false><<<grid, warps_per_block * 32, smem_bytes, s>>>(p);
+  main_qd<<<grid, warps_per_block * 32, smem_bytes, s>>>(p);
   return cudaGetLastError();
 }
 
