@@ -133,3 +133,54 @@ def test_n64_dense_samples(prec, ref3):
 def test_n128_dense_samples(prec, ref5):
     _check(prec, ref5)
 
+
+
+def _qd_reference(cfg, seed, pairs):
+    """Quad-double data of the workload (the double-double values with two
+    random lower parts) and exact rows at (point, polynomial) pairs."""
+    s, pts = synth.config(cfg)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sq, pq = s.to_qd(seed + 1), synth.widen_qd(rng, pts)
+    cols = sorted({q for q, _ in pairs})
+    sub = np.ascontiguousarray(pq[:, cols])
+    jobs = [(sq, sub, cols.index(q), [p]) for q, p in pairs]
+    with cf.ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(E.evaluate_point, *zip(*jobs)))
+    rows = []
+    for (sy, pt, c, (p,)), (f, J) in zip(jobs, res):
+        Sf, SJ = E.scales_point(sy, pt, c, polys=[p])
+        rows.append((pairs[len(rows)], (f[p], J[p], Sf[p], SJ[p])))
+    return {"system": sq, "pts": pq, "rows": rows}
+
+
+def _check_qd_rows(ref):
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+    from _util import QD_TOL
+
+    s, pts = ref["system"], ref["pts"]
+    P = pts.shape[1]
+    ev = pkg.PolyEval(s, pkg.PE_QD_INT, max_points=P)
+    f, J = ev.eval(torch.from_numpy(pts).cuda())
+    torch.cuda.synchronize()
+    assert ev.status() == pkg.PE_OK
+    for (q, p), (fx, Jx, sf, sj) in ref["rows"]:
+        fq = f[p, q].cpu().numpy()
+        Jq = J[p, :, q].cpu().numpy()
+        assert E.normwise_error(fq, fx, sf) <= QD_TOL, (q, p)
+        ej = max(E.normwise_error(Jq[i], Jx.get(i, E.ZERO), sj.get(i, 0.0)) for i in range(s.n_vars))
+        assert ej <= QD_TOL, (q, p, ej)
+    ev.close()
+
+
+def test_n64_quad_double_rows():
+    """Quad-double on the whole n = 64 batch (4096 points): rows at both ends
+    and in between against the exact oracle at 1e-60."""
+    _check_qd_rows(_qd_reference(3, 333, [(0, 0), (15, 63), (2047, 31), (4080, 7), (4095, 63), (4095, 0)]))
+
+
+def test_n128_quad_double_rows():
+    """Quad-double on the whole n = 128 batch (16384 points): rows at both
+    ends and in between against the exact oracle at 1e-60."""
+    _check_qd_rows(_qd_reference(5, 555, [(0, 0), (15, 127), (8191, 64), (16368, 5), (16383, 127), (16383, 0)]))
