@@ -283,10 +283,17 @@ PE_API int polyeval_newton(polyeval_t *h, void *points, int64_t P, void *out_f, 
 
 /*
  * polyeval_eval with HOST buffers: copies points to the device, evaluates,
- * and copies f and J back, all on `stream`, then synchronises the stream.
- * Host buffers should be pinned for full copy speed.  Device staging
- * buffers are allocated on the first call (and grown when P grows) and kept
- * by the handle.  Errors: as polyeval_eval, plus PE_ENOMEM.
+ * and copies f and J back, then synchronises.  When the outputs of the call
+ * exceed 512 MiB the points are split into C chunks (one per 256 MiB of
+ * outputs, at most 8, each of at least 1024 points): chunk c is evaluated on
+ * `stream` while the outputs of chunk c - 1 are copied to the host on a
+ * stream of the handle, so the copies hide behind the evaluation; each
+ * chunk's columns of the [.][P] host arrays are moved by one pitched copy.
+ * The results are those of polyeval_eval on the chunks' point counts.
+ * Host buffers should be pinned for full copy speed and for the overlap.
+ * Device staging buffers (two chunks' worth when split) are allocated on the
+ * first call (and grown when P grows) and kept by the handle.  Errors: as
+ * polyeval_eval, plus PE_ENOMEM.
  */
 PE_API int polyeval_eval_host(polyeval_t *h, const void *points, int64_t P, void *out_f, void *out_J, void *stream);
 

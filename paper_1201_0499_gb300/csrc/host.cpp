@@ -100,6 +100,10 @@ struct polyeval {
   DeviceBuf tr_xw[2], tr_xsw[2], tr_stw[2], tr_perm[2], tr_home, tr_list;
   DeviceBuf nt_Jdd, nt_fdd;  // quad-double Newton: double-double systems too large for shared memory
   cudaStream_t tr_stream = nullptr;  // the tracker's own stream (graph capture needs one)
+  // polyeval_eval_host over point chunks: the copies of chunk c run on this
+  // stream while chunk c + 1 is evaluated; two sets of staging buffers
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t chunk_done[2] = {}, chunk_copied[2] = {};
   struct Tuned {
     int64_t P;
     int chunks;
@@ -124,6 +128,11 @@ struct polyeval {
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
     if (tr_stream) cudaStreamDestroy(tr_stream);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    for (auto &e : chunk_done)
+      if (e) cudaEventDestroy(e);
+    for (auto &e : chunk_copied)
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -804,6 +813,17 @@ namespace {
 // the tuned table or the heuristic.
 // Monomial groups per warp for P points: enough that the lane pairs of a warp
 // are busy when P < 16 (the largest power of two G with G P <= 16).
+// Point chunks of polyeval_eval_host: one per 256 MiB of outputs, at most 8,
+// each of at least 1024 points (a chunk's evaluation then still fills the GPU).
+int host_chunks(const polyeval *h, int64_t P) {
+  const SysDesc &d = h->sys[0];
+  const size_t out = static_cast<size_t>(elem_doubles(h)) * sizeof(double) * static_cast<size_t>(P) *
+                     (static_cast<size_t>(d.N) + static_cast<size_t>(d.N) * d.n);
+  int C = static_cast<int>(std::min<size_t>(8, out >> 28));
+  while (C > 1 && P / C < 1024) C--;
+  return std::max(C, 1);
+}
+
 int default_groups(int64_t P) {
   int G = 1;
   while (G < 16 && 2 * G * P <= pe::kPointsPerWarp) G *= 2;
@@ -1191,18 +1211,67 @@ int polyeval_eval_host(polyeval_t *h, const void *points, int64_t P, void *out_f
   if (!points || !out_f || !out_J) return PE_EINVAL;
   const SysDesc &d = h->sys[0];
   const size_t eb = static_cast<size_t>(elem_doubles(h)) * sizeof(double);
-  const size_t bp = eb * d.n * static_cast<size_t>(P), bf = eb * d.N * static_cast<size_t>(P),
-               bj = eb * d.N * static_cast<size_t>(d.n) * static_cast<size_t>(P);
-  int rc;
-  if (h->stage_pts.bytes < bp && (rc = h->stage_pts.alloc(bp)) != PE_OK) return rc;
-  if (h->stage_f.bytes < bf && (rc = h->stage_f.alloc(bf)) != PE_OK) return rc;
-  if (h->stage_J.bytes < bj && (rc = h->stage_J.alloc(bj)) != PE_OK) return rc;
+  const int C = host_chunks(h, P);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemcpyAsync(h->stage_pts.p, points, bp, cudaMemcpyHostToDevice, s) != cudaSuccess) return PE_ECUDA;
-  if ((rc = polyeval_eval(h, h->stage_pts.p, P, h->stage_f.p, h->stage_J.p, stream)) != PE_OK) return rc;
-  if (bf && cudaMemcpyAsync(out_f, h->stage_f.p, bf, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PE_ECUDA;
-  if (bj && cudaMemcpyAsync(out_J, h->stage_J.p, bj, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PE_ECUDA;
-  return cudaStreamSynchronize(s) == cudaSuccess ? PE_OK : PE_ECUDA;
+  int rc;
+  if (C == 1) {
+    const size_t bp = eb * d.n * static_cast<size_t>(P), bf = eb * d.N * static_cast<size_t>(P),
+                 bj = eb * d.N * static_cast<size_t>(d.n) * static_cast<size_t>(P);
+    if ((rc = ensure(h->stage_pts, bp)) || (rc = ensure(h->stage_f, bf)) || (rc = ensure(h->stage_J, bj))) return rc;
+    if (cudaMemcpyAsync(h->stage_pts.p, points, bp, cudaMemcpyHostToDevice, s) != cudaSuccess) return PE_ECUDA;
+    if ((rc = polyeval_eval(h, h->stage_pts.p, P, h->stage_f.p, h->stage_J.p, stream)) != PE_OK) return rc;
+    if (bf && cudaMemcpyAsync(out_f, h->stage_f.p, bf, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PE_ECUDA;
+    if (bj && cudaMemcpyAsync(out_J, h->stage_J.p, bj, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PE_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? PE_OK : PE_ECUDA;
+  }
+  // C chunks of at most Pc points, two staging sets used in turn: chunk c is
+  // evaluated on `stream` while the outputs of chunk c - 1 go to the host on
+  // the copy stream.  Each chunk's columns of the [.][P] host arrays are one
+  // pitched copy.
+  const int64_t Pc = (P + C - 1) / C;
+  const size_t sp = eb * d.n * static_cast<size_t>(Pc), sf = eb * d.N * static_cast<size_t>(Pc),
+               sj = eb * d.N * static_cast<size_t>(d.n) * static_cast<size_t>(Pc);
+  if ((rc = ensure(h->stage_pts, 2 * sp)) || (rc = ensure(h->stage_f, 2 * sf)) || (rc = ensure(h->stage_J, 2 * sj)))
+    return rc;
+  if (!h->copy_stream && cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    h->copy_stream = nullptr;
+    return PE_ECUDA;
+  }
+  for (int b = 0; b < 2; b++) {
+    if (!h->chunk_done[b] && cudaEventCreateWithFlags(&h->chunk_done[b], cudaEventDisableTiming) != cudaSuccess)
+      return PE_ECUDA;
+    if (!h->chunk_copied[b] && cudaEventCreateWithFlags(&h->chunk_copied[b], cudaEventDisableTiming) != cudaSuccess)
+      return PE_ECUDA;
+  }
+  const size_t hp = eb * static_cast<size_t>(P);  // row pitch of the host arrays
+  rc = PE_OK;
+  for (int c = 0; c < C && rc == PE_OK; c++) {
+    const int64_t q0 = c * Pc, pc = std::min<int64_t>(Pc, P - q0);
+    if (pc <= 0) break;
+    const int b = c & 1;
+    char *spts = static_cast<char *>(h->stage_pts.p) + b * sp;
+    char *sff = static_cast<char *>(h->stage_f.p) + b * sf;
+    char *sJ = static_cast<char *>(h->stage_J.p) + b * sj;
+    const size_t w = eb * static_cast<size_t>(pc);
+    if (c >= 2 && cudaStreamWaitEvent(s, h->chunk_copied[b], 0) != cudaSuccess) rc = PE_ECUDA;  // staging b free
+    if (rc == PE_OK && cudaMemcpy2DAsync(spts, w, static_cast<const char *>(points) + eb * q0, hp, w, d.n,
+                                         cudaMemcpyHostToDevice, s) != cudaSuccess)
+      rc = PE_ECUDA;
+    if (rc == PE_OK) rc = polyeval_eval(h, spts, pc, sff, sJ, stream);
+    if (rc == PE_OK && (cudaEventRecord(h->chunk_done[b], s) != cudaSuccess ||
+                        cudaStreamWaitEvent(h->copy_stream, h->chunk_done[b], 0) != cudaSuccess))
+      rc = PE_ECUDA;
+    if (rc == PE_OK && d.N > 0 &&
+        (cudaMemcpy2DAsync(static_cast<char *>(out_f) + eb * q0, hp, sff, w, w, d.N, cudaMemcpyDeviceToHost,
+                           h->copy_stream) != cudaSuccess ||
+         cudaMemcpy2DAsync(static_cast<char *>(out_J) + eb * q0, hp, sJ, w, w, static_cast<size_t>(d.N) * d.n,
+                           cudaMemcpyDeviceToHost, h->copy_stream) != cudaSuccess))
+      rc = PE_ECUDA;
+    if (rc == PE_OK && cudaEventRecord(h->chunk_copied[b], h->copy_stream) != cudaSuccess) rc = PE_ECUDA;
+  }
+  const bool ok = cudaStreamSynchronize(h->copy_stream) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+  if (rc != PE_OK) return rc;
+  return ok ? PE_OK : PE_ECUDA;
 }
 
 int polyeval_cost(const polyeval_t *h, double *fp64_ops, double *fp64_flops) {

@@ -510,3 +510,36 @@ def test_monomial_groups_few_points(prec, P):
             check_exact_oracle(s, pts, f, J, tol(prec), dd=prec == "dd")
     g = ev.autotune(x)[2]
     assert g in (1, 2, 4, 8, 16)
+
+
+@pytest.mark.parametrize("prec,P", [("dd", 6200), ("ddint", 4101), ("f64", 8200)])
+def test_host_entry_point_in_chunks_matches_device(prec, P):
+    """polyeval_eval_host on outputs above 512 MiB splits the points into
+    chunks (here 3 chunks of 2067/2067/2066 points, 2 of 2051/2050, 2 of 4100) and
+    copies each chunk's columns to the host while the next is evaluated:
+    bit-identical to polyeval_eval on the device (each point's sums run in
+    monomial order whatever tile holds it)."""
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+    from _util import pe_precision
+
+    s, _ = synth.config(3, n_points=1)
+    pts = synth.points(132, s.n_vars, P, modulus_octaves=(-1, 0))
+    dd = prec != "f64"
+    sy = s if dd else s.as_fp64()
+    host_pts = np.ascontiguousarray(pts if dd else pts[..., [0, 2]])
+    c = host_pts.shape[-1]
+    ev = pkg.PolyEval(sy, pe_precision(prec), max_points=P)
+    f_dev, J_dev = ev.eval(torch.from_numpy(host_pts).cuda())
+    torch.cuda.synchronize()
+    hp = torch.from_numpy(host_pts).pin_memory()
+    hf = torch.full((s.n_polys, P, c), float("nan"), dtype=torch.float64).pin_memory()
+    hJ = torch.full((s.n_polys, s.n_vars, P, c), float("nan"), dtype=torch.float64).pin_memory()
+    for _ in range(2):  # the second call reuses the staging buffers and the handle's copy stream
+        pkg.polyeval_eval_host(ev.handle, hp, P, hf, hJ)
+        assert torch.equal(hf, f_dev.cpu()) and torch.equal(hJ, J_dev.cpu())
+        hf.fill_(float("nan"))
+        hJ.fill_(float("nan"))
+    assert ev.status() == pkg.PE_OK
+    ev.close()
