@@ -1011,7 +1011,12 @@ int set_batch_gcap(polyeval *h, int gcap) {
 int autotune_many(polyeval *h, const void *points, void *out_f, void *out_J, cudaStream_t s, int *chunks, int *shape,
                   int *groups) {
   if (!points || !out_f || !out_J || !arrays_aligned(points, out_f, out_J)) return PE_EINVAL;
-  if (h->n_items_batch == 0) return PE_OK;
+  if (h->n_items_batch == 0) {  // nothing to time: report the launch in place
+    if (chunks) *chunks = std::max(h->batch_chunks, 1);
+    if (shape) *shape = h->batch_mode > 0 ? h->batch_mode : 2;
+    if (groups) *groups = h->batch_gcap;
+    return PE_OK;
+  }
   const int64_t capacity = static_cast<int64_t>(h->sms) * h->blocks_per_sm_1;
   const size_t per_chunk = batch_outputs_bytes(h);
   const int max_c = per_chunk ? static_cast<int>(std::min<int64_t>(
