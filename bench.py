@@ -377,7 +377,8 @@ class Timer:
             fn()
             stops[i].record(self.stream)
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+        self.last = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+        return sum(self.last)
 
 
 def leg_ms(timer, wl, prec, warmup, reps, dist):
@@ -629,6 +630,7 @@ def main():
     torch.cuda.synchronize()
     t_wall0 = time.time()
     total_ms = timer.run(lambda: step(prim), args.steps)
+    step_ms = list(timer.last)
     t_wall1 = time.time()
     if dist is not None:
         dist.barrier()
@@ -705,6 +707,8 @@ def main():
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": ms_per_step,
+        "step_ms_median": statistics.median(step_ms),
+        "step_ms_min_max": [min(step_ms), max(step_ms)],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,

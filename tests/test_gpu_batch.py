@@ -187,3 +187,20 @@ def test_batch_cuda_graph_replay_matches_eager(prec):
     torch.cuda.synchronize()
     assert pkg.polyeval_status(many.handle) == pkg.PE_OK
     assert torch.equal(fb, f_ref) and torch.equal(Jb, J_ref)
+
+
+def test_batch_without_points_autotunes_and_evaluates():
+    """A batch whose systems all have no points: evaluation is a no-op and the
+    autotuner reports the launch in place."""
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+
+    systems, _ = _small_batch("dd")
+    many = pkg.PolyEvalMany(systems[:3], [0, 0, 0], pkg.PE_DD)
+    x = torch.zeros(2, 4, dtype=torch.float64, device="cuda")
+    chunks, shape, groups = pkg.polyeval_autotune(many.handle, x, 0, x, x)
+    assert chunks >= 1 and shape in (1, 2) and groups in (1, 16)
+    pkg.polyeval_eval_many(many.handle, x, x, x)
+    torch.cuda.synchronize()
+    assert pkg.polyeval_status(many.handle) == pkg.PE_OK
