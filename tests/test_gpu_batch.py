@@ -204,3 +204,97 @@ def test_batch_without_points_autotunes_and_evaluates():
     pkg.polyeval_eval_many(many.handle, x, x, x)
     torch.cuda.synchronize()
     assert pkg.polyeval_status(many.handle) == pkg.PE_OK
+
+
+@pytest.fixture(scope="module")
+def config4_rows():
+    """The 200-system workload with one seeded point per system (every
+    system has at least one point): the C double-double oracle's outputs at
+    that point on the double-double inputs and on the inputs rounded to
+    double, and the normwise scales."""
+    import concurrent.futures as cf
+    import os
+
+    import oracle
+
+    systems, pts = synth.config(4)
+    rng = np.random.Generator(np.random.PCG64(641))
+    qs = [int(rng.integers(0, x.shape[1])) for x in pts]
+
+    def one(args):  # one point per call: the systems run side by side on the host cores
+        s, x, q = args
+        sub = np.ascontiguousarray(x[:, q:q + 1])
+        s64, p64 = fp64_inputs(s, sub)
+        return q, oracle.dd_eval(s, sub, threads=1), oracle.dd_eval(s64, p64, threads=1), scales(s, sub)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        rows = list(ex.map(one, zip(systems, pts, qs)))
+    return systems, pts, rows
+
+
+@pytest.mark.parametrize("prec", ["dd", "ddint", "f64"])
+def test_config4_every_system_at_a_seeded_point(prec, config4_rows):
+    """Every one of the 200 systems, at one seeded point each, every output
+    (all polynomials, every J entry) against the C double-double oracle,
+    after the batch autotuner picked the launch."""
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+
+    systems, pts, rows = config4_rows
+    dd = prec != "f64"
+    many = pkg.PolyEvalMany([s if dd else s.as_fp64() for s in systems], [p.shape[1] for p in pts],
+                            pe_precision(prec))
+    pb, fb, Jb = many.buffers()
+    many.pack_points([to_device(p, dd) for p in pts], pb)
+    many.autotune(pb, fb, Jb)
+    many.eval_buffers(pb, fb, Jb)
+    torch.cuda.synchronize()
+    assert pkg.polyeval_status(many.handle) == pkg.PE_OK
+    fs, Js = many.views(fb, Jb)
+    for si, (q, ref_dd, ref_64, (Sf, SJ)) in enumerate(rows):
+        f = fs[si][:, q:q + 1].cpu().numpy()
+        J = Js[si][:, :, q:q + 1].cpu().numpy()
+        Fo, Jo = ref_dd if dd else ref_64
+        if not dd:
+            f, J = widen(f), widen(J)
+        assert normwise_vs(f, Fo, Sf) <= tol(prec), si
+        assert normwise_vs(J, Jo, SJ) <= tol(prec), si
+    many.close()
+
+
+def test_config4_quad_double_every_system_one_row():
+    """Quad-double on the 200-system batch: for every system one row (one
+    polynomial, all of its J entries) at a seeded point against the exact
+    oracle at 1e-60."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import torch
+
+    import paper_1201_0499_gb300 as pkg
+    from _util import QD_TOL
+
+    systems, pts = synth.config(4)
+    rng = np.random.Generator(np.random.PCG64(651))
+    qs = [s.to_qd(652 + i) for i, s in enumerate(systems)]
+    qp = [synth.widen_qd(rng, p) for p in pts]
+    picks = [(int(rng.integers(0, p.shape[1])), int(rng.integers(0, s.n_polys))) for s, p in zip(qs, qp)]
+    jobs = [(s, np.ascontiguousarray(p[:, q:q + 1]), 0, [poly]) for s, p, (q, poly) in zip(qs, qp, picks)]
+    with cf.ProcessPoolExecutor(max_workers=16, mp_context=mp.get_context("spawn")) as ex:
+        exact = list(ex.map(E.evaluate_point, *zip(*jobs)))
+    many = pkg.PolyEvalMany(qs, [p.shape[1] for p in qp], pkg.PE_QD_INT)
+    pb, fb, Jb = many.buffers()
+    many.pack_points([to_device(p) for p in qp], pb)
+    many.eval_buffers(pb, fb, Jb)
+    torch.cuda.synchronize()
+    assert pkg.polyeval_status(many.handle) == pkg.PE_OK
+    fs, Js = many.views(fb, Jb)
+    for si, ((q, poly), (f, J), job) in enumerate(zip(picks, exact, jobs)):
+        Sf, SJ = E.scales_point(job[0], job[1], 0, polys=[poly])
+        assert E.normwise_error(fs[si][poly, q].cpu().numpy(), f[poly], Sf[poly]) <= QD_TOL, si
+        Jrow = Js[si][poly, :, q].cpu().numpy()
+        ej = max(E.normwise_error(Jrow[i], J[poly].get(i, E.ZERO), SJ[poly].get(i, 0.0))
+                 for i in range(qs[si].n_vars))
+        assert ej <= QD_TOL, (si, ej)
+    many.close()
