@@ -543,6 +543,11 @@ def main():
     ap.add_argument("--no-secondary", action="store_true", help="skip the smaller workloads")
     ap.add_argument("--only-tracker", action="store_true",
                     help="run only the path-tracking leg and print its JSON object (for profiling the tracker)")
+    ap.add_argument("--only-newton", action="store_true",
+                    help="run only the Newton-step legs on the n = 32 workload and print their JSON object "
+                         "(for profiling the solve)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in launch of a smaller headline workload instead of autotuning it")
     ap.add_argument("--points", type=int, default=0,
                     help="evaluate only the first POINTS points of a single-system workload (profiling of "
                          "smaller launches; 0: all)")
@@ -576,6 +581,18 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
+    if args.only_newton:
+        wl2 = Workload(2, rank, dev)
+        timer2 = Timer(torch, stream, dev)
+        out = {}
+        for prec in ("dd", "qd"):
+            ms_eval = leg_ms(timer2, wl2, prec, 1, 3, dist)
+            out[prec] = newton_leg(pkg, torch, timer2, wl2, prec, ms_eval, 1, 3, dist, world)
+        if rank == 0:
+            print(json.dumps({"newton_step": out}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     cfg = args.config
     wl = Workload(cfg, rank, dev, host=True, points=args.points)
     prim = args.precision
@@ -585,13 +602,15 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
 
     tuned = {}
-    if cfg != CONFIG_INDEX:
+    if cfg != CONFIG_INDEX and not args.no_autotune:
         # pick the launch per precision on this batch, before any timed step
         for prec in PRECS:
             c, m, g = wl.autotune(prec, stream)
             tuned[prec] = {"chunks": c, "shape": "one wave" if m == 1 else "persistent", "groups": g}
         torch.cuda.synchronize()
         launch_note = "autotuned per precision (polyeval_autotune)"
+    elif cfg != CONFIG_INDEX:
+        launch_note = "built-in (autotuning skipped)"
     else:
         # 128 x 1024 (polynomial, tile) items fill many waves and one chunk of
         # outputs (8.7 GB) exceeds the chunk scratch: the tuner's only
