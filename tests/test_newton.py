@@ -181,3 +181,38 @@ def test_newton_rejects_non_square_and_batch():
     with pytest.raises(pkg.PolyEvalError) as e:
         pkg.polyeval_newton(many.handle, x, 4, x, x)
     assert e.value.code == pkg.PE_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["dd", "ddint", "f64"])
+def test_newton_step_on_the_n128_system(prec):
+    """One Newton step on the n = 128, m = 1024, k = 32 system at 48 points
+    (128 x 128 complex systems, solved in global memory by 32-lane segments):
+    at four of the points the normwise backward error of the GPU dx, measured
+    exactly against the C double-double oracle's f and J (themselves within
+    1e-30 of exact), is within the precision's bound."""
+    import oracle
+
+    s, pts = synth.config(5, n_points=48)
+    n = s.n_vars
+    if prec == "f64":
+        s, pts = s.as_fp64(), pts.copy()
+        pts[..., 1] = 0.0
+        pts[..., 3] = 0.0
+    _x1, dx, norms = run_newton(s, pts, prec)
+    sample = [0, 17, 40, 47]
+    Fo, Jo = oracle.dd_eval(s, np.ascontiguousarray(pts[:, sample]), threads=0)
+    for c, q in enumerate(sample):
+        f = [fr_dd(Fo[i, c]) for i in range(n)]
+        g = [fr_dd(dx[i, q]) for i in range(n)]
+        res, Jn = 0.0, 0.0
+        for i in range(n):
+            row = [fr_dd(Jo[i, j, c]) for j in range(n)]
+            acc = f[i]
+            for j in range(n):
+                acc = N.c_add(acc, N.c_mul(row[j], g[j]))
+            res = max(res, cabs(acc))
+            Jn = max(Jn, sum(cabs(v) for v in row))
+        gn = max(cabs(gi) for gi in g)
+        eta = res / (Jn * gn + max(cabs(fi) for fi in f))
+        assert eta <= BACKWARD_TOL[prec], (q, eta)
+        assert norms[q, 1] == pytest.approx(gn, rel=1e-12)
