@@ -57,8 +57,8 @@ DFMA_PER_SM_CLK = 2  # nominal FP64 FMA lanes per SM per clock on GB300
 # while they are summed), so it scales to the 16384-point launch by the points.
 # The figure belongs to the kernel sources it was taken on (their fingerprint,
 # kernel_sources_sha()); with other sources the line reports null.
-MAIN_TRAFFIC_PER_POINT = (19_217_836_800 + 35_688_403_200) / 512  # read + write bytes of the capture / points
-MAIN_TRAFFIC_SOURCES = "f37a39cfa853037a"
+MAIN_TRAFFIC_PER_POINT = (19_233_778_176 + 35_684_915_200) / 512  # read + write bytes of the capture / points
+MAIN_TRAFFIC_SOURCES = "daec4a2983d22163"
 KERNEL_SOURCES = ("kernels.cu", "dd.cuh", "arith.cuh", "items.cuh", "internal.h")
 
 

@@ -204,22 +204,21 @@ std::vector<int32_t> batch_item_words(const polyeval *h, int gcap) {
 
 // FP64 instructions and flops per point for one monomial (k variables, n2 of
 // them with exponent >= 2), as the main kernel executes them (both lanes of
-// a point).  Double-double, per lane: a product that feeds another product
-// (common factor, forward and backward chains) is a renormalised dot product,
-// 2 DMUL + 6 DFMA + 8 DADD = 16 instructions (22 flops); a final product
-// (value, derivatives) 2 DMUL + 6 DFMA + 5 DADD = 13 (19 flops); a sum 5 DADD;
-// an integer scale DMUL + 2 DFMA.  Double: a product DMUL + DFMA, a sum of J
-// one DADD, a compensated sum of f 4 DADD, a scale one DMUL.
+// a point).  Double-double, per lane: a chain product (common factor,
+// forward and backward chains) is a dot product of 2 DMUL + 6 DFMA + 5 DADD
+// = 13 instructions (19 flops), every kChainRenorm-th one renormalised by 3
+// DADD more; a final product (value, derivatives) 13; a sum 5 DADD; an
+// integer scale DMUL + 2 DFMA.  Double: a product DMUL + DFMA, a sum of J one
+// DADD, a compensated sum of f 4 DADD, a scale one DMUL.
 struct Cost {
   double ops = 0, flops = 0;
 };
 
 Cost monomial_cost(bool dd, int k, int n2) {
   if (k == 0) return dd ? Cost{10, 10} : Cost{8, 8};
-  // chains: common factor + forward products (n2 + k - 1), backward (k - 2);
-  // every second product of a chain is renormalised
+  // chains: common factor + forward products (n2 + k - 1), backward (k - 2)
   const int l1 = n2 + k - 1, l2 = k >= 2 ? k - 2 : 0;
-  const double renorm = l1 / 2 + l2 / 2;
+  const double renorm = l1 / pe::kChainRenorm + l2 / pe::kChainRenorm;
   const double plain = (l1 + l2) - renorm + (k >= 2 ? k : 1);  // + value and derivative products
   Cost c;
   if (dd) {

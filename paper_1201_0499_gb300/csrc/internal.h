@@ -15,6 +15,22 @@ constexpr int kWarpsPerBlockMax = 4;
 // its monomial groups per warp in bits 27..29 (groups > 1 for the last,
 // partial tile of a system with double-double or double arithmetic).
 constexpr int kTileBits = 27;
+// A product that feeds another product in a chain (common factor, forward
+// and backward products) is renormalised every kChainRenorm-th step only.
+// Left unnormalised, a complex double-double product's low word grows by at
+// most about 2.5 u of the product per step (the rounding of the high word,
+// the two exact product errors and the cross terms with the operands' low
+// words), so r steps after a renormalisation it is within about 2.5 r u.
+// What a product then drops -- the product of the low words (the factor read
+// from memory is normalised, so below 2.5 r u * u / 2) and the six roundings
+// of the low-word sums (each below u / 2 of a sum of at most 2.5 (r + 1) u) --
+// is of order 10 r u^2.  With r = 4 a chain of 85 products (k = 32, 24
+// exponents >= 2) stays within about 3e-29 of its value even if every error
+// has the same sign.  A renormalisation costs 3 FP64 instructions against 13
+// for the product, so every fourth step instead of every second saves about
+// 4 % of the evaluation's FP64 instructions.
+constexpr int kChainRenorm = 4;
+
 // Streaming-multiprocessor count of a GB300 (two dies of 76): the grids of
 // the grid-stride kernels are capped at a whole number of blocks per SM.
 // Launches whose balance depends on it query the device instead.

@@ -86,14 +86,13 @@ __device__ void process_item(const MainParams &kp, const Item &it, typename A::V
       continue;
     }
     const uint32_t *vw = kp.var + vb;
-    // Products in a chain are renormalised every second step: one
-    // unnormalised product leaves a low word of a few ulps, which the next
-    // product absorbs at O(u^2) cost; two in a row would let it grow.
-    bool renorm = false;
+    int step = 0;  // products since the last renormalisation (kChainRenorm)
     auto chain = [&](V y, const Full &X) {
-      const V r = renorm ? mul_x<A, true>(y, X, sgn, kFull) : mul_x<A, false>(y, X, sgn, kFull);
-      renorm = !renorm;
-      return r;
+      if (++step == kChainRenorm) {
+        step = 0;
+        return mul_x<A, true>(y, X, sgn, kFull);
+      }
+      return mul_x<A, false>(y, X, sgn, kFull);
     };
     // Stage 1: G = c * prod_{a_j >= 2} x_{i_j}^(a_j - 1)
     for (int j = 0; j < k; j++) {
@@ -116,7 +115,7 @@ __device__ void process_item(const MainParams &kp, const Item &it, typename A::V
     accumulate<A>(jel(vl), c, valid, al == 1 ? Pc : A::mul_int(Pc, int_as_double(al)));
     // Stage 2, backward: Q = x_{i_{j+2}} ... x_{i_k}; derivative by x_{i_{j+1}} = a_{j+1} slot_j Q
     V Q = A::comp(xl, c);
-    renorm = false;
+    step = 0;
     for (int j = k - 2; j >= 0; j--) {
       const uint32_t w = __ldg(vw + j);
       const int v = static_cast<int>(w & 0xffffu), a = static_cast<int>(w >> 16);
@@ -191,11 +190,13 @@ __device__ void process_item_groups(const MainParams &kp, const Item &it, typena
       if (k == 0) {
         f = A::f_add(f, Gv);
       } else {
-        bool renorm = false;
+        int step = 0;
         auto chain = [&](V y, const Full &Xf) {
-          const V r = renorm ? mul_x<A, true>(y, Xf, sgn, pm) : mul_x<A, false>(y, Xf, sgn, pm);
-          renorm = !renorm;
-          return r;
+          if (++step == kChainRenorm) {
+            step = 0;
+            return mul_x<A, true>(y, Xf, sgn, pm);
+          }
+          return mul_x<A, false>(y, Xf, sgn, pm);
         };
         for (int j = 0; j < k; j++) {
           const uint32_t w = __ldg(vw + j);
@@ -214,7 +215,7 @@ __device__ void process_item_groups(const MainParams &kp, const Item &it, typena
         f = A::f_add(f, mul_x<A, false>(Pc, xl, sgn, pm));
         // derivative terms into the slots: slot j <- term of x_{i_{j+1}}
         V Q = A::comp(xl, c);
-        renorm = false;
+        step = 0;
         for (int j = k - 2; j >= 0; j--) {
           const int a = static_cast<int>(__ldg(vw + j) >> 16);
           const V D = mul_split<A>(smem[j * 32 + lane], Q, c, sgn, pm);
