@@ -472,6 +472,20 @@ def test_c_dd_oracle_within_dd_tolerance(cfg):
     assert ef <= 1e-30 and ej <= 1e-30, (ef, ej)
 
 
+@pytest.mark.parametrize("cfg", [3, 5])
+def test_c_dd_oracle_within_dd_tolerance_on_large_shapes(cfg):
+    """The dense GPU samples of the n = 64 and n = 128 workloads are compared
+    with the C oracle; here the C oracle itself is held to 1e-30 of the exact
+    values (Section 2, Eq. 1) on the first and last polynomial at one point of
+    those shapes (k = 16 and 32, exponents up to 8 and 4)."""
+    import oracle
+
+    s, pts = synth.config(cfg, n_points=1)
+    F, J = oracle.dd_eval(s, pts, threads=2)
+    ef, ej = E.max_errors(s, pts, F, J, range(1), polys=[0, s.n_polys - 1])
+    assert ef <= 1e-30 and ej <= 1e-30, (ef, ej)
+
+
 def test_c_dd_oracle_point_range_and_args():
     import oracle
 
